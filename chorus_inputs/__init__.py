@@ -1,0 +1,196 @@
+"""Seeded synthetic inputs shared by the oracle and the CUDA path.
+
+This module holds only problem *inputs*: the node coordinates and 20-node
+connectivity of a cubed-sphere spherical-shell mesh, and the raw physical
+parameter sets of the shell workloads.  It contains none of the
+spectral-difference arithmetic (no points, bases, metrics, fluxes or
+time stepping); both the oracle and the GPU library compute all of that
+themselves from these inputs.
+
+Mesh (paper Section 3, Fig. 1; Section 5): all-hexahedral shell made of
+20-node iso-parametric elements (8 corners + 12 mid-edge nodes) with nodes
+uniformly distributed in radius.  The paper fuses eight GAMBIT segments; here
+the shell is a gnomonic equiangular cubed sphere, 6 panels x n x n lateral
+cells x n_r radial layers.  Mid-edge nodes sit at the mid-angle on the exact
+sphere (lateral edges) or at the mid-radius (radial edges).
+
+Local node order of a hexahedron (reference cube [0,1]^3, axes xi, eta, zeta):
+  corners  0:(0,0,0) 1:(1,0,0) 2:(1,1,0) 3:(0,1,0)
+           4:(0,0,1) 5:(1,0,1) 6:(1,1,1) 7:(0,1,1)
+  mid-edge 8:(h,0,0) 9:(1,h,0) 10:(h,1,0) 11:(0,h,0)
+           12:(h,0,1) 13:(1,h,1) 14:(h,1,1) 15:(0,h,1)
+           16:(0,0,h) 17:(1,0,h) 18:(1,1,h) 19:(0,1,h)      (h = 1/2)
+On the cubed sphere xi follows the first panel angle, eta the second and
+zeta the radius, which gives positive Jacobians on all six panels.
+"""
+from __future__ import annotations
+
+import dataclasses
+import math
+
+import numpy as np
+
+# reference-cube coordinates of the 20 nodes, in units of 1/2
+HEX20_REF2 = np.array(
+    [
+        [0, 0, 0], [2, 0, 0], [2, 2, 0], [0, 2, 0],
+        [0, 0, 2], [2, 0, 2], [2, 2, 2], [0, 2, 2],
+        [1, 0, 0], [2, 1, 0], [1, 2, 0], [0, 1, 0],
+        [1, 0, 2], [2, 1, 2], [1, 2, 2], [0, 1, 2],
+        [0, 0, 1], [2, 0, 1], [2, 2, 1], [0, 2, 1],
+    ],
+    dtype=np.int64,
+)
+
+
+def _panel_direction(panel: int, ta: np.ndarray, tb: np.ndarray) -> np.ndarray:
+    """Unnormalised direction of the gnomonic point (tan a, tan b) on a panel."""
+    one = np.ones_like(ta)
+    if panel == 0:
+        d = (one, ta, tb)
+    elif panel == 1:
+        d = (-ta, one, tb)
+    elif panel == 2:
+        d = (-one, -ta, tb)
+    elif panel == 3:
+        d = (ta, -one, tb)
+    elif panel == 4:
+        d = (-tb, ta, one)
+    elif panel == 5:
+        d = (tb, ta, -one)
+    else:
+        raise ValueError(panel)
+    return np.stack(d, axis=-1)
+
+
+def cubed_sphere_hex20(n: int, n_r: int, r_inner: float, r_outer: float):
+    """Return (node_xyz [n_nodes,3] float64, hex20 [E,20] int64).
+
+    Element order: e = ((panel*n + j)*n + i)*n_r + k with i, j the lateral
+    cell indices along the two panel angles and k the radial layer (fastest).
+    """
+    if n < 1 or n_r < 1 or not (0.0 < r_inner < r_outer):
+        raise ValueError("bad cubed-sphere parameters")
+    m = 2 * n  # fine lateral grid (corners + mid-edge points)
+    mr = 2 * n_r
+    ang = -math.pi / 4 + (math.pi / 2) * np.arange(m + 1) / m
+    tan = np.tan(ang)
+    tan[0], tan[-1] = -1.0, 1.0  # exact panel edges: shared edges match bitwise
+    radii = r_inner + (r_outer - r_inner) * np.arange(mr + 1) / mr
+    radii[-1] = r_outer
+
+    I, J, L = np.meshgrid(np.arange(m + 1), np.arange(m + 1), np.arange(mr + 1), indexing="ij")
+    keys = []
+    xyz = []
+    for panel in range(6):
+        d = _panel_direction(panel, tan[I], tan[J])
+        d = d / np.sqrt(d[..., 0] * d[..., 0] + d[..., 1] * d[..., 1] + d[..., 2] * d[..., 2])[..., None]
+        xyz.append(d * radii[L][..., None])
+    xyz = np.stack(xyz)  # [6, m+1, m+1, mr+1, 3]
+
+    # element -> fine-grid indices of its 20 nodes
+    E = 6 * n * n * n_r
+    pan, jj, ii, kk = np.meshgrid(np.arange(6), np.arange(n), np.arange(n), np.arange(n_r), indexing="ij")
+    pan, jj, ii, kk = (a.reshape(-1) for a in (pan, jj, ii, kk))
+    gi = 2 * ii[:, None] + HEX20_REF2[None, :, 0]
+    gj = 2 * jj[:, None] + HEX20_REF2[None, :, 1]
+    gk = 2 * kk[:, None] + HEX20_REF2[None, :, 2]
+    pts = xyz[pan[:, None], gi, gj, gk]  # [E,20,3]
+    assert pts.shape == (E, 20, 3)
+
+    # merge coincident nodes (shared between elements and across panel seams)
+    flat = pts.reshape(-1, 3)
+    scale = 2.0 ** 36 / r_outer
+    key = np.round(flat * scale).astype(np.int64)
+    uniq, inv = np.unique(key, axis=0, return_inverse=True)
+    inv = inv.reshape(-1)
+    node_xyz = np.zeros((uniq.shape[0], 3))
+    node_xyz[inv] = flat
+    hex20 = inv.reshape(E, 20).astype(np.int64)
+    return node_xyz, hex20
+
+
+@dataclasses.dataclass(frozen=True)
+class PhysParams:
+    """Raw physical parameters of a shell workload (nondimensional units).
+
+    R_o = 1, GM = 1, rho_c = 1, gas constant 1, gamma = 1 + 1/n (adiabatic
+    polytrope, Section 4.2), Omega = nu / (Ek d^2) (Eq. 24).  kappa_r = 0 and
+    a zero bottom flux, T_top = NaN meaning "polytrope temperature at r_o".
+    """
+
+    gamma: float
+    R_gas: float
+    GM: float
+    Omega: float
+    nu: float
+    kappa: float
+    kappa_r: float
+    poly_n: float
+    N_rho: float
+    rho_c: float
+    bottom_flux: float
+    T_top: float
+
+    def as_tuple(self):
+        return dataclasses.astuple(self)
+
+
+@dataclasses.dataclass(frozen=True)
+class ShellConfig:
+    name: str
+    n: int  # lateral cells per panel edge
+    n_r: int  # radial layers
+    p: int  # polynomial degree (N = p + 1 solution points per direction)
+    r_inner: float
+    r_outer: float
+    seed: int
+    entropy_amp: float
+    steps: int
+    phys: PhysParams
+
+    @property
+    def n_elem(self) -> int:
+        return 6 * self.n * self.n * self.n_r
+
+    @property
+    def n_dof(self) -> int:
+        return self.n_elem * (self.p + 1) ** 3
+
+
+def make_phys(beta: float, poly_n: float, N_rho: float, Ek: float, nu: float = 5e-4,
+              kappa: float = 5e-4) -> PhysParams:
+    d = 1.0 - beta
+    return PhysParams(
+        gamma=1.0 + 1.0 / poly_n,
+        R_gas=1.0,
+        GM=1.0,
+        Omega=nu / (Ek * d * d),
+        nu=nu,
+        kappa=kappa,
+        kappa_r=0.0,
+        poly_n=poly_n,
+        N_rho=N_rho,
+        rho_c=1.0,
+        bottom_flux=0.0,
+        T_top=float("nan"),
+    )
+
+
+# Shell workloads: cubed-sphere meshes 6 x n x n x n_r, polytrope n = 1.5,
+# seeded entropy perturbation.
+SHELL_288_P3 = ShellConfig("shell_288_p3", 4, 3, 3, 0.75, 1.0, 1, 1e-3, 100,
+                           make_phys(0.75, 1.5, 3.0, 1e-3))
+SHELL_331776_P3 = ShellConfig("shell_331776_p3", 48, 24, 3, 0.75, 1.0, 2, 1e-3, 1000,
+                              make_phys(0.75, 1.5, 3.0, 1e-3))
+SHELL_786432_P4 = ShellConfig("shell_786432_p4", 64, 32, 4, 0.71, 1.0, 3, 1e-3, 100,
+                              make_phys(0.71, 1.5, 4.0, 2.447e-3))
+
+CONFIGS = {c.name: c for c in (SHELL_288_P3, SHELL_331776_P3, SHELL_786432_P4)}
+
+
+def small_shell(n: int, n_r: int, p: int, seed: int = 7, amp: float = 1e-3, beta: float = 0.75,
+                N_rho: float = 3.0) -> ShellConfig:
+    """A small shell of the same family for tests."""
+    return ShellConfig(f"shell_{n}x{n_r}_p{p}", n, n_r, p, beta, 1.0, seed, amp, 10,
+                       make_phys(beta, 1.5, N_rho, 1e-3))

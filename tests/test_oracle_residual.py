@@ -1,0 +1,186 @@
+"""Pins of the oracle's residual and time stepping against what the paper fixes.
+
+  * freestream preservation on the curved shell (Eq. 12 with the curl-form metrics)
+  * discrete conservation of mass, and of energy up to the gravity work (Eq. 4 in
+    conservative form, single-valued common fluxes, walls with V_r = 0)
+  * hydrostatic balance of the polytrope (Eqs. 20, 25-27) converging under
+    refinement, and failing with the opposite gravity sign (a planted mistake)
+  * convergence of the residual to the exact right-hand side of Eqs. 1-3 on a
+    manufactured solution, built symbolically in tests/mms.py
+  * Rusanov consistency and symmetry, SSP-RK3 order
+"""
+import dataclasses
+import math
+
+import numpy as np
+import pytest
+
+import mms
+from chorus_inputs import cubed_sphere_hex20, make_phys
+from oracle import rk, state
+from oracle.physics import Physics, conserved, inviscid_flux, rusanov
+from oracle.residual import Discretization, residual
+
+
+def _disc(n, n_r, p, ri=0.75):
+    xyz, h20 = cubed_sphere_hex20(n, n_r, ri, 1.0)
+    return Discretization(xyz, h20, p, ri, 1.0)
+
+
+def _phys(nu=5e-4, kappa=5e-4, N_rho=3.0, **kw):
+    ph = Physics.from_params(make_phys(0.75, 1.5, N_rho, 1e-3, nu=nu, kappa=kappa), 0.75, 1.0)
+    return dataclasses.replace(ph, **kw) if kw else ph
+
+
+def _weights(disc):
+    g = disc.geometry(np.arange(disc.n_elem))
+    w = disc.ops.w
+    return w[None, :, None, None] * w[None, None, :, None] * w[None, None, None, :] * g["detJ"], g
+
+
+@pytest.mark.parametrize("p", [2, 3])
+@pytest.mark.parametrize("viscous", [False, True])
+def test_freestream_preservation(p, viscous):
+    n_r = 5
+    disc = _disc(2, n_r, p)
+    ph = _phys(nu=1e-2 if viscous else 0.0, kappa=1e-2 if viscous else 0.0, GM=0.0, Omega=0.0)
+    N, E = disc.N, disc.n_elem
+    u = np.broadcast_to(np.array([0.3, -0.2, 0.1]), (E, N, N, N, 3))
+    Q = np.moveaxis(conserved(np.full((E, N, N, N), 1.3), u, np.full((E, N, N, N), 0.9), ph), -1, 1).copy()
+    R = residual(disc, ph, Q)
+    k = np.arange(E) % n_r
+    hops = 2 if viscous else 1  # walls break the uniform state; BR1 reaches two face hops
+    interior = (k >= hops) & (k < n_r - hops)
+    h_min = state.min_edge_chord(disc.node_xyz, disc.hex20)
+    scale = np.abs(inviscid_flux(np.moveaxis(Q[0, :, 0, 0, 0], 0, -1), ph)).max() * N * N / h_min
+    assert np.abs(R[interior]).max() < 1e-13 * scale
+    # and the walls do act on the wall layers (the check above is not vacuous)
+    assert np.abs(R[k == 0]).max() > 1e-3
+
+
+def test_mass_and_energy_conservation():
+    disc = _disc(3, 3, 3)
+    W, g = _weights(disc)
+    ph = _phys(nu=2e-3, kappa=0.0)
+    Q = state.initial_state(ph, g["x"], seed=11, amp=1e-2)
+    rng = np.random.default_rng(0)
+    Q[:, 1:4] += 0.01 * Q[:, :1] * rng.standard_normal(Q[:, 1:4].shape)  # nonzero velocities, walls active
+    R = residual(disc, ph, Q)
+    mass = np.sum(W * R[:, 0])
+    assert abs(mass) < 1e-13 * np.sum(W * np.abs(R[:, 0]))
+    # energy: walls carry no energy flux (V_r = 0, u.tau.n = 0, f = 0 for kappa = 0),
+    # so the total energy changes only by the gravity work -sum(M_5)
+    x = np.moveaxis(g["x"], 1, -1)
+    r = np.linalg.norm(x, axis=-1)
+    work = np.sum(np.moveaxis(Q[:, 1:4], 1, -1) * (-ph.GM * x / r[..., None] ** 3), axis=-1)  # m.g
+    dE = np.sum(W * R[:, 4])
+    assert abs(dE - np.sum(W * work)) < 1e-12 * np.sum(W * np.abs(R[:, 4]))
+
+
+def _hydro_norm(n, p, flip_gravity=False):
+    disc = _disc(n, n, p)
+    ph = _phys(N_rho=1.0)
+    W, g = _weights(disc)
+    Q0 = state.background(ph, g["x"])
+    ph_eval = dataclasses.replace(ph, GM=-ph.GM, T_top=ph.T_wall_top) if flip_gravity else ph
+    R0 = residual(disc, ph_eval, Q0)
+    x = np.moveaxis(g["x"], 1, -1)
+    rho_g = Q0[:, 0] * ph.GM / np.sum(x * x, axis=-1)  # magnitude of the balanced terms
+    return math.sqrt(np.sum(W * np.sum(R0[:, 1:4] ** 2, axis=1))) / math.sqrt(np.sum(W * rho_g ** 2))
+
+
+def test_hydrostatic_balance_converges():
+    errs = [_hydro_norm(n, 3) for n in (2, 4, 8)]
+    rates = [math.log2(errs[i] / errs[i + 1]) for i in range(2)]
+    assert errs[-1] < 3e-4
+    assert rates[-1] > 2.5  # the residual truncation error of SD falls as h^p
+
+
+def test_hydrostatic_balance_fails_with_wrong_gravity_sign():
+    # planted mistake: gravity pointing outward leaves an O(rho g) momentum residual
+    assert _hydro_norm(4, 3, flip_gravity=True) > 1.0
+
+
+def _mms_error(n, n_r, p, ph, amp=0.05):
+    disc = _disc(n, n_r, p)
+    W, g = _weights(disc)
+    x = np.moveaxis(g["x"], 1, -1)
+    Q, L = mms.evaluate(ph, x, amp)
+    R = residual(disc, ph, np.moveaxis(Q, -1, 1).copy())
+    L = np.moveaxis(L, -1, 1)
+    k = np.arange(disc.n_elem) % n_r
+    sel = (k >= n_r // 3) & (k < 2 * n_r // 3)  # the same middle third of the shell at both sizes
+    err = np.sqrt(np.sum(W[sel][:, None] * (R[sel] - L[sel]) ** 2, axis=(0, 2, 3, 4)))
+    scale = np.sqrt(np.sum(W[sel][:, None] * L[sel] ** 2, axis=(0, 2, 3, 4)))
+    return err, scale
+
+
+@pytest.mark.parametrize("p,viscous", [(3, False), (3, True), (2, True)])
+def test_manufactured_solution_convergence(p, viscous):
+    nu = 2e-2 if viscous else 0.0
+    ph = _phys(nu=nu, kappa=nu, N_rho=1.0, Omega=1.0)
+    e1, _ = _mms_error(4, 6, p, ph)
+    e2, s2 = _mms_error(8, 12, p, ph)
+    rates = np.log2(e1 / e2)
+    # inviscid residual truncation falls as h^p; the lifted (BR1) second derivatives lose up to one order
+    assert np.all(rates > (p - 1.3 if viscous else p - 0.5)), rates
+    assert np.all(e2 < 0.05 * s2), (e2, s2)
+
+
+def test_manufactured_solution_catches_heat_flux_sign():
+    # planted mistake: the opposite diffusive-flux sign (Eq. 7 as printed) stops the energy equation converging
+    ph = _phys(nu=0.0, kappa=2e-2, N_rho=1.0, Omega=1.0)
+    bad = dataclasses.replace(ph, kappa=-ph.kappa)
+    x_err = []
+    for n, n_r in ((4, 6), (8, 12)):
+        disc = _disc(n, n_r, 3)
+        W, g = _weights(disc)
+        x = np.moveaxis(g["x"], 1, -1)
+        Q, L = mms.evaluate(ph, x, 0.05)
+        R = residual(disc, bad, np.moveaxis(Q, -1, 1).copy())
+        k = np.arange(disc.n_elem) % n_r
+        sel = (k >= n_r // 3) & (k < 2 * n_r // 3)
+        x_err.append(math.sqrt(np.sum(W[sel] * (R[sel, 4] - L[sel][..., 4]) ** 2)))
+    assert x_err[1] > 0.5 * x_err[0]  # no convergence
+
+
+def test_rusanov_consistency_and_symmetry():
+    ph = _phys()
+    rng = np.random.default_rng(5)
+    rho = 0.5 + rng.random(20)
+    u = 0.2 * rng.standard_normal((20, 3))
+    p = 0.1 + rng.random(20)
+    QL = conserved(rho, u, p, ph)
+    QR = conserved(rho[::-1].copy(), u[::-1].copy(), p[::-1].copy(), ph)
+    n = rng.standard_normal((20, 3))
+    n /= np.linalg.norm(n, axis=-1, keepdims=True)
+    F = np.einsum("...n,...nv->...v", n, inviscid_flux(QL, ph))
+    assert np.allclose(rusanov(QL, QL, n, ph), F, atol=1e-15)
+    assert np.allclose(rusanov(QL, QR, n, ph), -rusanov(QR, QL, -n, ph), atol=1e-15)
+
+
+def test_ssprk3_third_order(monkeypatch):
+    lam = -1.3 + 0.4j
+
+    monkeypatch.setattr(rk, "residual", lambda disc, ph, q: lam * q)
+    errs = []
+    for nsteps in (20, 40, 80):
+        y = rk.run(None, None, np.array([1.0 + 0j]), 1.0 / nsteps, nsteps)
+        errs.append(abs(y[0] - np.exp(lam)))
+    rates = [math.log2(errs[i] / errs[i + 1]) for i in range(2)]
+    assert min(rates) > 2.9
+
+
+def test_initial_state_entropy_perturbation():
+    disc = _disc(2, 2, 3)
+    _, g = _weights(disc)
+    ph = _phys()
+    amp = 1e-3
+    Q0 = state.background(ph, g["x"])
+    Q = state.initial_state(ph, g["x"], seed=5, amp=amp)
+    # pressure unchanged, fluid at rest, S'/C_p in [-A, A) with S = C_p ln(p^(1/gamma)/rho) (Eq. 23)
+    assert np.array_equal(Q[:, 4], Q0[:, 4]) and not np.any(Q[:, 1:4])
+    p = (ph.gamma - 1) * Q[:, 4]
+    dS = np.log(p ** (1 / ph.gamma) / Q[:, 0]) - np.log(p ** (1 / ph.gamma) / Q0[:, 0])
+    assert dS.max() <= amp * (1 + 1e-12) and dS.min() >= -amp * (1 + 1e-12)
+    assert abs(dS.mean()) < 0.1 * amp and dS.std() > 0.5 * amp
