@@ -1,0 +1,334 @@
+#!/usr/bin/env python
+"""Benchmark: RK-stage DOF updates per second of the SD residual + SSP-RK3 update on a shell.
+
+Default workload: the 331,776-element p=3 shell (6 x 48 x 48 x 24 cubed sphere, 21,233,664
+solution points x 5 variables), FP32 perturbation path, SSP-RK3.  One bench step = one SSP-RK3
+time step = 3 passes of the whole residual + stage update; the metric counts solution-point DOF
+updates per stage (DOF = elements x N^3, Eq. 19).
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl chorus|reference] [--prec fp32|fp64]
+
+--impl reference times the plain FP64 CPU oracle (the only reference implementation: the paper
+ships no code) on the host cores, on a bounded sample of the same workload.
+Under torchrun each rank runs an independent replica (the path is not sharded); the value is the
+total over ranks and the time the maximum over ranks.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "RK-stage DOF updates/s (p=3 shell), FP32 vs FP64 GPU at stated L2 error"
+UNIT = "DOF-stage/s"
+# algorithmic bytes per RK-stage DOF update at p=3: FP32 state traffic (read u^(k), read u^n on two of
+# three stages, write: 13.3 words) + FP32 stored metrics (|J|, grad xi at the solution points and
+# one metric row per flux point: 21.25 words) = 34.6 words = 138 B
+ALG_BYTES_PER_DOF_STAGE = {2: 141.0, 3: 138.0, 4: 137.0, 5: 135.0}
+ALG_BYTES_PER_DOF_STAGE_FP64 = {2: 283.0, 3: 277.0, 4: 273.0, 5: 271.0}
+
+
+def _dist():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+def _peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(path) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clock / throttle sampling during the timed region."""
+
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,clocks_event_reasons.hw_slowdown,"
+              "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+              "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "100"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.thread = threading.Thread(target=self._read, daemon=True)
+            self.thread.start()
+        except Exception:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.thread.join(timeout=2)
+        sm, mx, reasons = [], [], set()
+        names = ("hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap")
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 8:
+                continue
+            try:
+                sm.append(float(parts[0]))
+                mx.append(float(parts[1]))
+            except ValueError:
+                continue
+            for nm, val in zip(names, parts[4:8]):
+                if val.lower() == "active":
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def run_reference(args, cfg):
+    """The FP64 CPU oracle on a bounded sample of the workload (residual + stage update)."""
+    import numpy as np
+
+    from chorus_inputs import cubed_sphere_hex20
+    from oracle.physics import Physics
+    from oracle.residual import Discretization, residual
+    from oracle import state as ostate
+
+    xyz, h20 = cubed_sphere_hex20(cfg.n, cfg.n_r, cfg.r_inner, cfg.r_outer)
+    disc = Discretization(xyz, h20, cfg.p, cfg.r_inner, cfg.r_outer)
+    ph = Physics.from_params(cfg.phys, cfg.r_inner, cfg.r_outer)
+    N = cfg.p + 1
+    n_sample = min(disc.n_elem, args.ref_elems)
+    elems = np.arange(n_sample)
+    patch = disc.conn.closure(disc.conn.closure(elems))
+    Q = np.zeros((disc.n_elem, 5, N, N, N))
+    Q[patch] = ostate.initial_state(ph, disc.geometry(patch)["x"], cfg.seed, cfg.entropy_amp, elems=patch)
+    dt = 1e-3
+
+    def one_stage():
+        R = residual(disc, ph, Q, elems)
+        return Q[elems] + dt * R
+
+    for _ in range(max(0, args.warmup)):
+        one_stage()
+    times = []
+    for _ in range(args.steps):
+        t0 = time.perf_counter()
+        one_stage()
+        times.append(time.perf_counter() - t0)
+    units = n_sample * N ** 3
+    value = units * len(times) / sum(times)
+    return value, times, n_sample
+
+
+def main():
+    from chorus_inputs import CONFIGS
+
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=50)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="chorus", choices=["chorus", "reference"])
+    ap.add_argument("--prec", default="fp32", choices=["fp32", "fp64"])
+    ap.add_argument("--config", default="shell_331776_p3", choices=sorted(CONFIGS))
+    ap.add_argument("--fp64-steps", type=int, default=2)
+    ap.add_argument("--e2e-steps", type=int, default=5)
+    ap.add_argument("--ref-elems", type=int, default=256)
+    ap.add_argument("--cpu-seconds", type=float, default=12.0)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    cfg = CONFIGS[args.config]
+    rank, world, local = _dist()
+    N = cfg.p + 1
+
+    if args.impl == "reference":
+        if rank != 0:
+            return
+        value, times, n_sample = run_reference(args, cfg)
+        line = {
+            "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * statistics.mean(times),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "config": {"workload": cfg.name, "elements": cfg.n_elem, "p": cfg.p},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
+                             "sample": f"one residual + stage update on elements 0..{n_sample - 1} of {cfg.name} "
+                                       f"per step (numpy, single thread)"},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+        }
+        print(json.dumps(line))
+        return
+
+    import torch
+
+    torch.cuda.set_device(local)
+    if world > 1:
+        import torch.distributed as dist
+
+        dist.init_process_group("nccl")
+    from paper_1503_00834_gb300 import FP32_PERT, FP64, Shell, build as _build
+
+    _build.build()
+    prec = FP32_PERT if args.prec == "fp32" else FP64
+    tdt = torch.float32 if prec == FP32_PERT else torch.float64
+    stream = torch.cuda.current_stream()
+    sh = Shell(cfg)
+    mesh = sh.mesh
+    shape = mesh.state_shape()
+    Q = torch.empty(shape, dtype=tdt, device="cuda")
+    ws = torch.empty(mesh.workspace_bytes(prec), dtype=torch.uint8, device="cuda")
+    mesh.prepare(sh.params)
+    mesh.state_init(sh.params, cfg.seed, cfg.entropy_amp, prec, Q)
+    n_dof = cfg.n_dof
+
+    def barrier():
+        if world > 1:
+            torch.distributed.barrier()
+
+    # ---- warm-up, then K timed steps (inputs far larger than L2: state 425 MB FP32)
+    mesh.rk_step(sh.params, prec, Q, ws, sh.dt, max(3, args.warmup))
+    torch.cuda.synchronize()
+    barrier()
+    torch.cuda.synchronize()
+    clk = ClockSampler(local)
+    clk.start()
+    mesh.timing_enable(True)
+    mesh.timing_read()  # clear
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    ev0.record(stream)
+    mesh.rk_step(sh.params, prec, Q, ws, sh.dt, args.steps)
+    ev1.record(stream)
+    torch.cuda.synchronize()
+    barrier()
+    torch.cuda.synchronize()
+    clocks = clk.stop()
+    kms, kcnt = mesh.timing_read()
+    mesh.timing_enable(False)
+    ms = ev0.elapsed_time(ev1)
+    if world > 1:
+        t = torch.tensor([ms], device="cuda")
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        ms = float(t.item())
+    stages = 3 * args.steps
+    value = world * n_dof * stages / (ms / 1e3)
+    mesh.check()
+
+    # ---- dominant kernel roofline (residual + stage update kernel)
+    names = ["k_trace", "k_grad", "k_resid"]
+    dom = max(range(3), key=lambda c: kms[c])
+    per_launch_ms = kms[dom] / max(1, kcnt[dom])
+    alg = (ALG_BYTES_PER_DOF_STAGE if prec == FP32_PERT else ALG_BYTES_PER_DOF_STAGE_FP64)[cfg.p]
+    peak, peak_kind = _peaks()
+    achieved = alg * n_dof / (per_launch_ms / 1e3) / 1e9
+    traffic = None
+    prof = os.path.join(ROOT, "profiles", "traffic.json")
+    if os.path.exists(prof):
+        try:
+            with open(prof) as f:
+                tr = json.load(f)
+            key = f"{names[dom]}:{cfg.name}:{args.prec}"
+            traffic = tr.get(key)
+        except Exception:
+            traffic = None
+
+    # ---- FP64 GPU path on the same workload (the metric compares both)
+    fp64_value = None
+    if prec == FP32_PERT and args.fp64_steps > 0:
+        Q64 = torch.empty(shape, dtype=torch.float64, device="cuda")
+        ws64 = torch.empty(mesh.workspace_bytes(FP64), dtype=torch.uint8, device="cuda")
+        mesh.state_init(sh.params, cfg.seed, cfg.entropy_amp, FP64, Q64)
+        mesh.rk_step(sh.params, FP64, Q64, ws64, sh.dt, 1)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        mesh.rk_step(sh.params, FP64, Q64, ws64, sh.dt, args.fp64_steps)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        fp64_value = world * n_dof * 3 * args.fp64_steps / (e0.elapsed_time(e1) / 1e3)
+        del Q64, ws64
+
+    # ---- end to end through the public API with host buffers: H2D state, K steps, D2H state
+    host = torch.empty(shape, dtype=tdt, pin_memory=True)
+    host.copy_(Q)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    e0.record(stream)
+    for _ in range(args.e2e_steps):
+        Q.copy_(host, non_blocking=True)
+        mesh.rk_step(sh.params, prec, Q, ws, sh.dt, 1)
+        host.copy_(Q, non_blocking=True)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    e2e_ms = e0.elapsed_time(e1)
+    e2e_value = world * n_dof * 3 * args.e2e_steps / (e2e_ms / 1e3)
+    state_bytes = Q.numel() * Q.element_size()
+
+    # ---- CPU baseline: the oracle on a bounded sample, rank 0 at N=1 only
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        class _A:
+            pass
+
+        a = _A()
+        a.ref_elems, a.warmup = args.ref_elems, 1
+        a.steps = 1
+        t0 = time.perf_counter()
+        v, times, n_sample = run_reference(a, cfg)
+        per = times[0]
+        a.steps = max(1, int(args.cpu_seconds / max(per, 1e-3)))
+        v, times, n_sample = run_reference(a, cfg)
+        cpu = {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle",
+               "sample": f"{len(times)} x (residual + stage update) on elements 0..{n_sample - 1} of {cfg.name} "
+                         f"(numpy FP64, single thread), {sum(times):.1f} s"}
+
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": max(3, args.warmup), "ms_per_step": ms / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32" if prec == FP32_PERT else "f64",
+            "data": "synthetic",
+            "config": {"workload": cfg.name, "elements": cfg.n_elem, "p": cfg.p, "dof": n_dof,
+                       "precision": "FP32 perturbation + FP64 background" if prec == FP32_PERT else "FP64",
+                       "step": "one SSP-RK3 step = 3 residual + stage-update passes",
+                       "l2": "inputs larger than L2 (state %.0f MB)" % (state_bytes / 1e6),
+                       "parallelism": f"replicas x{world}"},
+            "fp64_gpu_value": fp64_value,
+            "roofline": {"bound": "hbm", "kernel": names[dom], "achieved": achieved, "peak": peak, "unit": "GB/s",
+                         "frac": achieved / peak, "traffic": traffic, "peak_kind": peak_kind,
+                         "alg_bytes_per_dof_stage": alg, "launch_ms": per_launch_ms,
+                         "stage_frac": alg * n_dof / (ms / stages / 1e3) / 1e9 / peak},
+            "kernel_ms": {names[c]: kms[c] for c in range(3)},
+            "kernel_launches": {names[c]: kcnt[c] for c in range(3)},
+            "gpu_launches": int(sum(kcnt)),
+            "clocks": clocks,
+            "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": state_bytes,
+                    "d2h_bytes_per_step": state_bytes},
+            "cpu_baseline": cpu,
+        }
+        print(json.dumps(line))
+    if world > 1:
+        torch.distributed.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -186,7 +186,11 @@ SHELL_331776_P3 = ShellConfig("shell_331776_p3", 48, 24, 3, 0.75, 1.0, 2, 1e-3, 
 SHELL_786432_P4 = ShellConfig("shell_786432_p4", 64, 32, 4, 0.71, 1.0, 3, 1e-3, 100,
                               make_phys(0.71, 1.5, 4.0, 2.447e-3))
 
-CONFIGS = {c.name: c for c in (SHELL_288_P3, SHELL_331776_P3, SHELL_786432_P4)}
+# a mid-size shell of the same family (state 126 MB in FP32, working set > L2) for profiling captures
+SHELL_98304_P3 = ShellConfig("shell_98304_p3", 32, 16, 3, 0.75, 1.0, 2, 1e-3, 100,
+                             make_phys(0.75, 1.5, 3.0, 1e-3))
+
+CONFIGS = {c.name: c for c in (SHELL_288_P3, SHELL_331776_P3, SHELL_786432_P4, SHELL_98304_P3)}
 
 
 def small_shell(n: int, n_r: int, p: int, seed: int = 7, amp: float = 1e-3, beta: float = 0.75,

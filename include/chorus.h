@@ -1,0 +1,143 @@
+/*
+ * chorus.h - C ABI of the GB300 spectral-difference (SD) residual library.
+ *
+ * The library evaluates the semi-discrete residual of the compressible
+ * Navier-Stokes equations for a stratified, rotating spherical shell (gravity
+ * g = -GM r_hat / r^2, Coriolis force about +z; paper Section 2, Eqs. 1-9)
+ * discretised by the spectral difference method on curved 20-node hexahedra
+ * (Section 3, Eqs. 10-19), with impenetrable stress-free walls (Section 5),
+ * and advances it with the three-stage SSP Runge-Kutta scheme.
+ *
+ * Conventions shared by every call
+ *  - p is the polynomial degree, N = p + 1 solution points per direction,
+ *    N^3 solution points per element.  2 <= p <= 5.
+ *  - State layout: Q[e][v][i + N*j + N*N*k] (element-major, then the five
+ *    conserved variables rho, rho u, rho v, rho w, E, then the solution point
+ *    with i along xi fastest).  Solution points are the Chebyshev-Gauss points
+ *    of Eq. 13 in each direction of the reference cube [0,1]^3.
+ *  - Precision:
+ *      CHORUS_FP64       Q holds the total conserved state, double.
+ *      CHORUS_FP32_PERT  Q holds the perturbation q' = Q - Q0 from the
+ *                        polytropic background Q0 (Eqs. 25-27 at rest), float.
+ *                        The background residual R(Q0) and the background
+ *                        tables are kept in FP64-derived form by the library.
+ *    Residuals R are dQ/dt in the same precision as Q (total, not
+ *    perturbation, for both precisions).
+ *  - Device pointers (Q, R, workspace) are caller-owned, contiguous, 16-byte
+ *    aligned device allocations.  Host pointers are marked "host".
+ *  - stream is a cudaStream_t passed as void* (NULL = legacy default stream).
+ *    Calls are asynchronous on that stream except where stated.
+ *  - Errors: arguments are validated before any launch (CHORUS_EINVAL,
+ *    CHORUS_EMESH); a CUDA error from a launch or copy returns CHORUS_ECUDA;
+ *    a device-side timeout of a bounded wait is reported as CHORUS_ETIMEOUT
+ *    by the next call that synchronises (chorus_reduce, chorus_check).
+ *    No call aborts the process or traps the GPU.
+ */
+#ifndef CHORUS_H
+#define CHORUS_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct chorus_mesh_s* chorus_mesh;
+
+typedef enum {
+  CHORUS_OK = 0,
+  CHORUS_EINVAL = 1,      /* bad argument */
+  CHORUS_ENOMEM = 2,      /* device or host allocation failed */
+  CHORUS_ECUDA = 3,       /* CUDA runtime error */
+  CHORUS_EMESH = 4,       /* invalid connectivity, non-manifold face, |J| <= 0, stray boundary */
+  CHORUS_ENAN = 5,        /* non-finite value found by a reduction */
+  CHORUS_ETIMEOUT = 6,    /* a bounded device-side wait ran out */
+  CHORUS_EUNSUPPORTED = 7 /* order or mode not built */
+} chorus_status;
+
+typedef enum { CHORUS_FP64 = 0, CHORUS_FP32_PERT = 1 } chorus_precision;
+
+/* Physical parameters (paper Section 2, Eq. 24, Section 4.2, Section 5), nondimensional.
+ * gamma, R_gas: ideal gas (Eq. 22); GM: gravity g = GM/r^2; Omega: rotation about +z;
+ * nu: kinematic viscosity (mu = rho nu, Eq. 9); kappa: entropy diffusivity; kappa_r: thermal
+ * diffusivity (f = -kappa rho T grad S - kappa_r rho C_p grad T); poly_n, N_rho, rho_c:
+ * polytrope of Eqs. 25-27 (beta = r_inner / r_outer from the mesh); bottom_flux: f.r_hat
+ * imposed on the inner wall (L / (4 pi R_i^2)); T_top: temperature imposed on the outer wall,
+ * NaN meaning the polytrope temperature at r_outer. */
+typedef struct {
+  double gamma, R_gas, GM, Omega;
+  double nu, kappa, kappa_r;
+  double poly_n, N_rho, rho_c;
+  double bottom_flux, T_top;
+} chorus_params;
+
+/* Build a mesh handle from 20-node hexahedra (Section 3 iso-parametric map, Section 5 20-node
+ * elements).  node_xyz: host [n_nodes][3] double.  hex20: host [n_elem][20] int64, 0-based,
+ * local node order: corners (0,0,0) (1,0,0) (1,1,0) (0,1,0) (0,0,1) (1,0,1) (1,1,1) (0,1,1),
+ * then the mid-edge nodes of edges 0-1, 1-2, 2-3, 3-0, 4-5, 5-6, 6-7, 7-4, 0-4, 1-5, 2-6, 3-7
+ * (reference axes xi, eta, zeta).  Faces are paired by their corner nodes; unpaired faces must lie
+ * on the sphere r_inner (inner wall) or r_outer (outer wall) to a relative 1e-6, else
+ * CHORUS_EMESH.  metric_mode 0: conservative curl-form metrics (freestream preserving for every
+ * p); 1: analytic cofactors of the 20-node map (freestream preserving for p >= 3).  The library
+ * copies what it needs; the caller keeps ownership of its arrays.  Synchronises the stream. */
+chorus_status chorus_mesh_create(int64_t n_nodes, const double* node_xyz, int64_t n_elem,
+                                 const int64_t* hex20, int p, double r_inner, double r_outer,
+                                 int metric_mode, void* stream, chorus_mesh* out);
+chorus_status chorus_mesh_destroy(chorus_mesh mesh);
+
+/* n_dof = n_elem * N^3 (Eq. 19); n_faces = interior faces + wall faces; h_min = shortest
+ * corner-to-corner element edge; volume = sum of w_i w_j w_k |J| (host outputs, any may be NULL). */
+chorus_status chorus_mesh_info(chorus_mesh mesh, int64_t* n_dof, int64_t* n_faces, double* h_min,
+                               double* volume);
+
+/* Build the per-parameter background tables (polytropic Q0, its FP64 residual R(Q0), lifted
+ * background density gradient, background face traces, gravity vectors).  Must be called before
+ * FP32_PERT residual/rk calls and before chorus_state_init; calling again with other parameters
+ * rebuilds them.  Allocates device memory owned by the mesh handle. */
+chorus_status chorus_prepare(chorus_mesh mesh, const chorus_params* params, void* stream);
+
+/* Seeded initial state (Section 4): the polytrope at rest with an entropy perturbation
+ * S'/C_p = A xi, xi in [-1,1) from SplitMix64(seed XOR g) at global solution point
+ * g = e N^3 + (i + N j + N^2 k); pressure kept, rho = rho_a exp(-A xi).  Q: device, layout above,
+ * in the given precision (total state for FP64, perturbation for FP32_PERT). */
+chorus_status chorus_state_init(chorus_mesh mesh, const chorus_params* params, uint64_t seed,
+                                double entropy_amp, chorus_precision prec, void* Q, void* stream);
+
+/* dQ/dt of the SD discretisation at the solution points (Sections 3 and 5).  Q, R: device.
+ * Needs chorus_rk_workspace_bytes() of scratch, passed as workspace. */
+chorus_status chorus_residual(chorus_mesh mesh, const chorus_params* params, chorus_precision prec,
+                              const void* Q, void* R, void* workspace, void* stream);
+
+/* Bytes of device scratch needed by chorus_residual and chorus_rk_step. */
+size_t chorus_rk_workspace_bytes(chorus_mesh mesh, chorus_precision prec);
+
+/* n_steps SSP-RK3 steps of size dt, in place on Q (Shu-Osher form:
+ * u1 = u + dt L(u); u2 = 3/4 u + 1/4 (u1 + dt L(u1)); u^{n+1} = 1/3 u + 2/3 (u2 + dt L(u2))). */
+chorus_status chorus_rk_step(chorus_mesh mesh, const chorus_params* params, chorus_precision prec,
+                             void* Q, void* workspace, double dt, int64_t n_steps, void* stream);
+
+/* FP64 volume integrals of Q (total state): out[0] mass, out[1] total energy, out[2] kinetic
+ * energy sum |m|^2/(2 rho), out[3] |L| with L = integral of x cross (rho u) (Section 6, Eq. 32).
+ * out: host double[4].  Synchronises the stream; returns CHORUS_ENAN on non-finite results. */
+chorus_status chorus_reduce(chorus_mesh mesh, const chorus_params* params, chorus_precision prec,
+                            const void* Q, double* out, void* stream);
+
+/* Kernel timing for measurement.  While enabled, every kernel that chorus_residual and
+ * chorus_rk_step launch is bracketed by a pair of CUDA events recorded on the call's stream (the
+ * kernels themselves are unchanged).  chorus_timing_read synchronises the stream and returns, per
+ * kernel class (0: face traces, 1: lifted gradients / one-sided viscous fluxes, 2: residual and RK
+ * update), the summed device milliseconds and launch counts recorded since the last read, then
+ * clears them.  ms, counts: host arrays of 3.  enable = 0 stops recording. */
+chorus_status chorus_timing_enable(chorus_mesh mesh, int enable);
+chorus_status chorus_timing_read(chorus_mesh mesh, void* stream, double* ms, int64_t* counts);
+
+/* Synchronise the stream and report a pending device-side error flag (CHORUS_ETIMEOUT). */
+chorus_status chorus_check(chorus_mesh mesh, void* stream);
+
+const char* chorus_strerror(chorus_status status);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* CHORUS_H */

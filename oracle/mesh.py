@@ -92,20 +92,31 @@ class Connectivity:
         self.wall[bnd_e[inner], bnd_f[inner]] = 1
         self.wall[bnd_e[outer], bnd_f[outer]] = 2
 
-        # point correspondence from physical coordinates
-        nodes = node_xyz[hex20]
+        self._node_xyz, self._hex20 = node_xyz, hex20
+        self._r_outer = r_outer
+        self._have_perm = np.zeros(E, dtype=bool)
+
+    def ensure_perm(self, elems: np.ndarray) -> None:
+        """Fill perm[e] for the given elements from physical coordinates (computed on first use)."""
+        elems = np.asarray(elems, dtype=np.int64)
+        todo = elems[~self._have_perm[elems]]
+        if todo.size == 0:
+            return
+        N = self.N
+        xyz, h20 = self._node_xyz, self._hex20
         for fa_ in range(6):
             for fb_ in range(6):
-                sel = np.nonzero((self.nbr[:, fa_] >= 0) & (self.nbr_face[:, fa_] == fb_))[0]
+                sel = todo[(self.nbr[todo, fa_] >= 0) & (self.nbr_face[todo, fa_] == fb_)]
                 for c0 in range(0, sel.size, 8192):
                     s = sel[c0:c0 + 8192]
-                    pa = _face_points(nodes[s], N, fa_)  # [S,N2,3]
-                    pb = _face_points(nodes[self.nbr[s, fa_]], N, fb_)
+                    pa = _face_points(xyz[h20[s]], N, fa_)  # [S,N2,3]
+                    pb = _face_points(xyz[h20[self.nbr[s, fa_]]], N, fb_)
                     dist = np.linalg.norm(pa[:, :, None, :] - pb[:, None, :, :], axis=-1)
                     match = np.argmin(dist, axis=2)
-                    if np.max(np.min(dist, axis=2)) > 1e-9 * r_outer:
+                    if np.max(np.min(dist, axis=2)) > 1e-9 * self._r_outer:
                         raise ValueError("face points of paired faces do not coincide")
                     self.perm[s, fa_] = match
+        self._have_perm[todo] = True
 
     def closure(self, elems: np.ndarray) -> np.ndarray:
         """elems plus all their face neighbours (sorted, unique)."""

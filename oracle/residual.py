@@ -134,6 +134,7 @@ def residual(disc: Discretization, ph: Physics, Q: np.ndarray, elems=None) -> np
     elems = np.asarray(elems, dtype=np.int64)
     S1 = conn.closure(elems)
     S2 = conn.closure(S1)
+    conn.ensure_perm(S2)
     loc = np.full(E, -1, dtype=np.int64)
     loc[S2] = np.arange(S2.size)
     gamma = ph.gamma

@@ -45,10 +45,13 @@ def background(ph: Physics, x: np.ndarray) -> np.ndarray:
     return Q0
 
 
-def initial_state(ph: Physics, x: np.ndarray, seed: int, amp: float) -> np.ndarray:
+def initial_state(ph: Physics, x: np.ndarray, seed: int, amp: float, elems=None) -> np.ndarray:
+    """Initial state at the solution points x [E,3,N,N,N] of elements `elems` (default 0..E-1)."""
     E = x.shape[0]
     N = x.shape[2]
-    g = np.arange(E * N ** 3, dtype=np.uint64).reshape(E, N, N, N)
+    elems = np.arange(E) if elems is None else np.asarray(elems)
+    g = (elems.astype(np.uint64)[:, None, None, None] * np.uint64(N ** 3)
+         + np.arange(N ** 3, dtype=np.uint64).reshape(N, N, N)[None])
     xi = uniform_pm1(seed, g)
     Q = background(ph, x)
     Q[:, 0] = Q[:, 0] * np.exp(-amp * xi)

@@ -1,0 +1,676 @@
+// C-ABI of the spectral-difference library (declared in include/chorus.h): mesh handle, background
+// preparation, seeded initial state, residual, SSP-RK3 stepping and FP64 reductions.
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <cmath>
+#include <cstring>
+#include <new>
+#include <vector>
+
+#include "../../include/chorus.h"
+#include "internal.h"
+#include "mesh_builder.h"
+#include "sd_tables.h"
+
+using namespace chorus;
+
+struct chorus_mesh_s {
+  int p = 0, N = 0;
+  int64_t E = 0;
+  double r_inner = 0, r_outer = 0;
+  HostMesh host;
+  Tables1D tab;
+  LaunchSet L{};
+  OpsArg<double> ops64{};
+  OpsArg<float> ops32{};
+  // device mesh arrays
+  int* d_nbr = nullptr;
+  int* d_code = nullptr;
+  double* d_Sf64 = nullptr;
+  double* d_invJ64 = nullptr;
+  double* d_x64 = nullptr;
+  double* d_wJ = nullptr;  // w_i w_j w_k |J| at the solution points (reductions)
+  float* d_Sf32 = nullptr;
+  float* d_invJ32 = nullptr;
+  float* d_x32 = nullptr;
+  unsigned* d_err = nullptr;
+  // prepared background
+  bool prepared = false;
+  chorus_params prep{};
+  double* d_Q0 = nullptr;     // [E][5][N3] FP64 polytrope at rest
+  float* d_bg = nullptr;      // [E][2][N3]
+  float* d_grho0 = nullptr;   // [E][3][N3]
+  float* d_bgT = nullptr;     // [E][6][2][N2]
+  float* d_R0 = nullptr;      // [E][5][N3]
+  double* d_red = nullptr;    // reduction partials
+  // measurement: event pairs around launches while timing is enabled
+  struct Rec {
+    int cls;
+    cudaEvent_t a, b;
+  };
+  bool timing = false;
+  std::vector<Rec> recs;
+  std::vector<cudaEvent_t> pool;
+};
+
+namespace {
+
+template <class T>
+cudaError_t dev_alloc(T** p, size_t count) {
+  return cudaMalloc((void**)p, count * sizeof(T) + 16);
+}
+
+void dev_free(void* p) {
+  if (p) cudaFree(p);
+}
+
+template <class R>
+MeshArg<R> mesh_arg(const chorus_mesh_s* m);
+template <>
+MeshArg<double> mesh_arg<double>(const chorus_mesh_s* m) {
+  return MeshArg<double>{(int)m->E, m->d_nbr, m->d_code, m->d_Sf64, m->d_invJ64, m->d_x64};
+}
+template <>
+MeshArg<float> mesh_arg<float>(const chorus_mesh_s* m) {
+  return MeshArg<float>{(int)m->E, m->d_nbr, m->d_code, m->d_Sf32, m->d_invJ32, m->d_x32};
+}
+
+template <class R>
+PhysArg<R> phys_arg(const chorus_params& P, double r_inner, double r_outer) {
+  PhysArg<R> a{};
+  const double gamma = P.gamma;
+  // polytrope of Eqs. 25-27; p_c from hydrostatic balance dp/dr = -rho GM / r^2 (Eq. 20)
+  const double beta = r_inner / r_outer, d = r_outer - r_inner, n = P.poly_n;
+  const double chi_o = (beta + 1.0) / (beta * std::exp(P.N_rho / n) + 1.0);
+  const double c = (2.0 * chi_o - beta - 1.0) / (1.0 - beta);
+  const double alpha = (1.0 + beta) * (1.0 - chi_o) / ((1.0 - beta) * (1.0 - beta));
+  const double p_c = P.GM * P.rho_c / ((n + 1.0) * alpha * d);
+  const double T_c = p_c / (P.R_gas * P.rho_c);
+  const double T_top = std::isnan(P.T_top) ? T_c * (c + alpha * d / r_outer) : P.T_top;
+  a.gamma = (R)gamma;
+  a.gm1 = (R)(gamma - 1.0);
+  a.Rgas = (R)P.R_gas;
+  a.CpR = (R)(gamma / (gamma - 1.0));
+  a.kappa = (R)P.kappa;
+  a.kappa_r = (R)P.kappa_r;
+  a.nu = (R)P.nu;
+  a.GM = (R)P.GM;
+  a.twoOmega = (R)(2.0 * P.Omega);
+  a.T_top = (R)T_top;
+  a.bottom_flux = (R)P.bottom_flux;
+  a.chi_c = c;
+  a.chi_ad = alpha * d;
+  a.rho_c = P.rho_c;
+  a.p_c = p_c;
+  a.poly_n = n;
+  return a;
+}
+
+bool params_ok(const chorus_params* P) {
+  return P && P->gamma > 1.0 && P->R_gas > 0 && P->GM > 0 && P->nu >= 0 && P->kappa >= 0 && P->kappa_r >= 0 &&
+         P->poly_n > 0 && P->N_rho > 0 && P->rho_c > 0 && std::isfinite(P->Omega) && std::isfinite(P->bottom_flux);
+}
+
+chorus_status cu(cudaError_t e) { return e == cudaSuccess ? CHORUS_OK : CHORUS_ECUDA; }
+
+#define CHK(x)                                   \
+  do {                                           \
+    cudaError_t _e = (x);                        \
+    if (_e != cudaSuccess) return CHORUS_ECUDA;  \
+  } while (0)
+
+// ---------------------------------------------------------------- small kernels
+
+// polytrope at rest at the solution points (FP64)
+__global__ void k_background(int64_t n_pts, int N3, const double* __restrict__ x, PhysArg<double> ph,
+                             double* __restrict__ Q0) {
+  const int64_t g = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (g >= n_pts) return;
+  const int64_t e = g / N3, pt = g % N3;
+  const double x0 = x[(e * 3 + 0) * N3 + pt], x1 = x[(e * 3 + 1) * N3 + pt], x2 = x[(e * 3 + 2) * N3 + pt];
+  const double r = sqrt(x0 * x0 + x1 * x1 + x2 * x2);
+  const double chi = ph.chi_c + ph.chi_ad / r;
+  const double rho = ph.rho_c * pow(chi, ph.poly_n);
+  const double p = ph.p_c * pow(chi, ph.poly_n + 1.0);
+  double* Qe = Q0 + e * 5 * N3;
+  Qe[pt] = rho;
+  Qe[N3 + pt] = 0.0;
+  Qe[2 * N3 + pt] = 0.0;
+  Qe[3 * N3 + pt] = 0.0;
+  Qe[4 * N3 + pt] = p / (double)ph.gm1;
+}
+
+__device__ __forceinline__ uint64_t splitmix64(uint64_t x) {
+  uint64_t z = x + 0x9E3779B97F4A7C15ull;
+  z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+  z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+  return z ^ (z >> 31);
+}
+
+// seeded entropy perturbation: rho = rho0 exp(-A xi), p and u unchanged (Section 4)
+__global__ void k_init(int64_t n_pts, int N3, const double* __restrict__ Q0, uint64_t seed, double amp, int fp32,
+                       double* __restrict__ q64, float* __restrict__ q32) {
+  const int64_t g = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (g >= n_pts) return;
+  const int64_t e = g / N3, pt = g % N3;
+  const uint64_t z = splitmix64(seed ^ (uint64_t)g);
+  const double xi = (double)(z >> 11) * 0x1.0p-53 * 2.0 - 1.0;
+  const double rho0 = Q0[e * 5 * N3 + pt];
+  if (fp32) {
+    float* qe = q32 + e * 5 * N3;
+    qe[pt] = (float)(rho0 * expm1(-amp * xi));
+    for (int v = 1; v < 5; ++v) qe[v * N3 + pt] = 0.0f;
+  } else {
+    double* qe = q64 + e * 5 * N3;
+    qe[pt] = rho0 * exp(-amp * xi);
+    for (int v = 1; v < 4; ++v) qe[v * N3 + pt] = 0.0;
+    qe[4 * N3 + pt] = Q0[e * 5 * N3 + 4 * N3 + pt];
+  }
+}
+
+__global__ void k_d2f(int64_t n, const double* __restrict__ a, float* __restrict__ b) {
+  const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (i < n) b[i] = (float)a[i];
+}
+
+// background tables of the perturbation form from the FP64 background state and its traces
+__global__ void k_bg_tables(int64_t E, int N3, int N2, const double* __restrict__ Q0, const double* __restrict__ T,
+                            float* __restrict__ bg, float* __restrict__ bgT) {
+  const int64_t g = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (g < E * N3) {
+    const int64_t e = g / N3, pt = g % N3;
+    bg[(e * 2) * N3 + pt] = (float)Q0[(e * 5) * N3 + pt];
+    bg[(e * 2 + 1) * N3 + pt] = (float)Q0[(e * 5 + 4) * N3 + pt];
+  }
+  if (g < E * 6 * N2) {
+    const int64_t ef = g / N2, t = g % N2;
+    bgT[(ef * 2) * N2 + t] = (float)T[(ef * 5) * N2 + t];
+    bgT[(ef * 2 + 1) * N2 + t] = (float)T[(ef * 5 + 4) * N2 + t];
+  }
+}
+
+// deterministic two-level FP64 reduction: per-block partial sums of
+// (mass, energy, kinetic, Lx, Ly, Lz), then one block sums the partials in a fixed order
+template <class R>
+__global__ void k_reduce_partial(int64_t n_pts, int N3, const R* __restrict__ q, const double* __restrict__ Q0,
+                                 const double* __restrict__ wJ, const double* __restrict__ x, double* __restrict__ part) {
+  __shared__ double sh[6][256];
+  double acc[6] = {0, 0, 0, 0, 0, 0};
+  for (int64_t g = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; g < n_pts; g += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t e = g / N3, pt = g % N3;
+    double Q[5];
+    for (int v = 0; v < 5; ++v) {
+      Q[v] = (double)q[(e * 5 + v) * N3 + pt];
+      if (Q0) Q[v] += Q0[(e * 5 + v) * N3 + pt];
+    }
+    const double w = wJ[g];
+    const double x0 = x[(e * 3) * N3 + pt], x1 = x[(e * 3 + 1) * N3 + pt], x2 = x[(e * 3 + 2) * N3 + pt];
+    acc[0] += w * Q[0];
+    acc[1] += w * Q[4];
+    acc[2] += w * 0.5 * (Q[1] * Q[1] + Q[2] * Q[2] + Q[3] * Q[3]) / Q[0];
+    acc[3] += w * (x1 * Q[3] - x2 * Q[2]);
+    acc[4] += w * (x2 * Q[1] - x0 * Q[3]);
+    acc[5] += w * (x0 * Q[2] - x1 * Q[1]);
+  }
+  for (int c = 0; c < 6; ++c) sh[c][threadIdx.x] = acc[c];
+  __syncthreads();
+  for (int s = blockDim.x / 2; s > 0; s >>= 1) {
+    if (threadIdx.x < s)
+      for (int c = 0; c < 6; ++c) sh[c][threadIdx.x] += sh[c][threadIdx.x + s];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0)
+    for (int c = 0; c < 6; ++c) part[blockIdx.x * 6 + c] = sh[c][0];
+}
+
+__global__ void k_reduce_final(int nb, const double* __restrict__ part, double* __restrict__ out) {
+  if (threadIdx.x < 6) {
+    double s = 0;
+    for (int b = 0; b < nb; ++b) s += part[b * 6 + threadIdx.x];
+    out[threadIdx.x] = s;
+  }
+}
+
+constexpr int kRedBlocks = 1024;
+
+template <class R>
+void fill_ops(const Tables1D& T, OpsArg<R>* o) {
+  std::memset(o, 0, sizeof(*o));
+  const int N = T.N;
+  for (int f = 0; f <= N; ++f)
+    for (int s = 0; s < N; ++s) o->I[f][s] = (R)T.I[f * N + s];
+  for (int s = 0; s < N; ++s)
+    for (int f = 0; f <= N; ++f) {
+      o->D[s][f] = (R)T.D[s * (N + 1) + f];
+      o->Lfs[s][f] = (R)T.Lfs[s * (N + 1) + f];
+    }
+  for (int i = 0; i < N; ++i)
+    for (int s = 0; s < N; ++s) o->Dsol[i][s] = (R)T.Dsol[i * N + s];
+  for (int s = 0; s < N; ++s) o->w[s] = (R)T.w[s];
+}
+
+void free_background(chorus_mesh_s* m) {
+  dev_free(m->d_Q0);
+  dev_free(m->d_bg);
+  dev_free(m->d_grho0);
+  dev_free(m->d_bgT);
+  dev_free(m->d_R0);
+  m->d_Q0 = nullptr;
+  m->d_bg = m->d_grho0 = m->d_bgT = m->d_R0 = nullptr;
+  m->prepared = false;
+}
+
+cudaEvent_t take_event(chorus_mesh_s* m) {
+  if (!m->pool.empty()) {
+    cudaEvent_t e = m->pool.back();
+    m->pool.pop_back();
+    return e;
+  }
+  cudaEvent_t e = nullptr;
+  if (cudaEventCreate(&e) != cudaSuccess) return nullptr;
+  return e;
+}
+
+void release_records(chorus_mesh_s* m) {
+  for (auto& r : m->recs) {
+    m->pool.push_back(r.a);
+    m->pool.push_back(r.b);
+  }
+  m->recs.clear();
+}
+
+// Runs one launch; with timing enabled, brackets it with events on the stream.
+template <class Fn>
+cudaError_t timed(chorus_mesh_s* m, int cls, cudaStream_t st, Fn&& fn) {
+  if (!m->timing) return fn();
+  cudaEvent_t a = take_event(m), b = take_event(m);
+  if (!a || !b) return cudaErrorMemoryAllocation;
+  cudaError_t e = cudaEventRecord(a, st);
+  if (e == cudaSuccess) e = fn();
+  if (e == cudaSuccess) e = cudaEventRecord(b, st);
+  m->recs.push_back({cls, a, b});
+  return e;
+}
+
+void free_mesh(chorus_mesh_s* m) {
+  release_records(m);
+  for (cudaEvent_t e : m->pool) cudaEventDestroy(e);
+  m->pool.clear();
+  free_background(m);
+  dev_free(m->d_nbr);
+  dev_free(m->d_code);
+  dev_free(m->d_Sf64);
+  dev_free(m->d_invJ64);
+  dev_free(m->d_x64);
+  dev_free(m->d_wJ);
+  dev_free(m->d_Sf32);
+  dev_free(m->d_invJ32);
+  dev_free(m->d_x32);
+  dev_free(m->d_err);
+  dev_free(m->d_red);
+  delete m;
+}
+
+size_t ws_words(const chorus_mesh_s* m) {
+  const size_t N = m->N, E = m->E;
+  const size_t N2 = N * N, N3 = N2 * N;
+  // stage buffer + two trace buffers + viscous normal-flux traces
+  return E * 5 * N3 + 2 * E * 6 * 5 * N2 + E * 6 * 4 * N2;
+}
+
+template <class R>
+struct Ws {
+  R* s;
+  R* Ta;
+  R* Tb;
+  R* Tv;
+};
+
+template <class R>
+Ws<R> split_ws(const chorus_mesh_s* m, void* w) {
+  const size_t N = m->N, E = m->E;
+  const size_t N2 = N * N, N3 = N2 * N;
+  R* p = (R*)w;
+  Ws<R> r;
+  r.s = p;
+  r.Ta = r.s + E * 5 * N3;
+  r.Tb = r.Ta + E * 6 * 5 * N2;
+  r.Tv = r.Tb + E * 6 * 5 * N2;
+  return r;
+}
+
+BgArg bg_arg(const chorus_mesh_s* m) { return BgArg{m->d_bg, m->d_grho0, m->d_bgT, m->d_R0}; }
+
+bool same_params(const chorus_params& a, const chorus_params& b) {
+  const double* x = &a.gamma;
+  const double* y = &b.gamma;
+  for (size_t i = 0; i < sizeof(chorus_params) / sizeof(double); ++i)
+    if (!(x[i] == y[i] || (std::isnan(x[i]) && std::isnan(y[i])))) return false;
+  return true;
+}
+
+inline dim3 grid1(int64_t n, int bs = 256) { return dim3((unsigned)((n + bs - 1) / bs)); }
+
+}  // namespace
+
+extern "C" {
+
+const char* chorus_strerror(chorus_status s) {
+  switch (s) {
+    case CHORUS_OK: return "ok";
+    case CHORUS_EINVAL: return "invalid argument";
+    case CHORUS_ENOMEM: return "out of memory";
+    case CHORUS_ECUDA: return "CUDA error";
+    case CHORUS_EMESH: return "invalid mesh";
+    case CHORUS_ENAN: return "non-finite value";
+    case CHORUS_ETIMEOUT: return "device wait timed out";
+    case CHORUS_EUNSUPPORTED: return "unsupported";
+  }
+  return "unknown status";
+}
+
+chorus_status chorus_mesh_create(int64_t n_nodes, const double* node_xyz, int64_t n_elem, const int64_t* hex20, int p,
+                                 double r_inner, double r_outer, int metric_mode, void* stream, chorus_mesh* out) {
+  if (!out) return CHORUS_EINVAL;
+  *out = nullptr;
+  if (p < 2 || p > 5) return CHORUS_EUNSUPPORTED;
+  chorus_mesh_s* m = new (std::nothrow) chorus_mesh_s();
+  if (!m) return CHORUS_ENOMEM;
+  m->p = p;
+  m->N = p + 1;
+  m->E = n_elem;
+  m->r_inner = r_inner;
+  m->r_outer = r_outer;
+  m->tab = make_tables(m->N);
+  const char* why = "";
+  const int rc = build_mesh(n_nodes, node_xyz, n_elem, hex20, p, r_inner, r_outer, metric_mode, m->tab, &m->host, &why);
+  if (rc != 0) {
+    delete m;
+    return (chorus_status)rc;
+  }
+  switch (p) {
+    case 2: m->L = launchers_p2(); break;
+    case 3: m->L = launchers_p3(); break;
+    case 4: m->L = launchers_p4(); break;
+    default: m->L = launchers_p5(); break;
+  }
+  fill_ops(m->tab, &m->ops64);
+  fill_ops(m->tab, &m->ops32);
+  const int N = m->N, N2 = N * N, N3 = N2 * N;
+  const size_t E = (size_t)n_elem;
+  const size_t nS = E * 9 * (N + 1) * N2, nP = E * N3;
+  cudaStream_t st = (cudaStream_t)stream;
+  std::vector<double> wJ(nP), invJ(nP);
+  for (size_t e = 0; e < E; ++e)
+    for (int k = 0; k < N; ++k)
+      for (int j = 0; j < N; ++j)
+        for (int i = 0; i < N; ++i) {
+          const size_t g = e * N3 + i + N * j + N2 * k;
+          wJ[g] = m->tab.w[i] * m->tab.w[j] * m->tab.w[k] * m->host.detJ[g];
+          invJ[g] = 1.0 / m->host.detJ[g];
+        }
+  std::vector<float> f32(nS);
+  bool ok = dev_alloc(&m->d_nbr, E * 6) == cudaSuccess && dev_alloc(&m->d_code, E * 6) == cudaSuccess &&
+            dev_alloc(&m->d_Sf64, nS) == cudaSuccess && dev_alloc(&m->d_invJ64, nP) == cudaSuccess &&
+            dev_alloc(&m->d_x64, 3 * nP) == cudaSuccess && dev_alloc(&m->d_wJ, nP) == cudaSuccess &&
+            dev_alloc(&m->d_Sf32, nS) == cudaSuccess && dev_alloc(&m->d_invJ32, nP) == cudaSuccess &&
+            dev_alloc(&m->d_x32, 3 * nP) == cudaSuccess && dev_alloc(&m->d_err, 4) == cudaSuccess &&
+            dev_alloc(&m->d_red, (size_t)kRedBlocks * 6 + 8) == cudaSuccess;
+  if (!ok) {
+    free_mesh(m);
+    return CHORUS_ENOMEM;
+  }
+  cudaError_t ce = cudaSuccess;
+  auto up = [&](void* d, const void* h, size_t bytes) {
+    if (ce == cudaSuccess) ce = cudaMemcpyAsync(d, h, bytes, cudaMemcpyHostToDevice, st);
+    if (ce == cudaSuccess) ce = cudaStreamSynchronize(st);  // host buffers are reused below
+  };
+  up(m->d_nbr, m->host.nbr.data(), E * 6 * sizeof(int));
+  up(m->d_code, m->host.code.data(), E * 6 * sizeof(int));
+  up(m->d_Sf64, m->host.Sf.data(), nS * sizeof(double));
+  up(m->d_invJ64, invJ.data(), nP * sizeof(double));
+  up(m->d_x64, m->host.x.data(), 3 * nP * sizeof(double));
+  up(m->d_wJ, wJ.data(), nP * sizeof(double));
+  for (size_t i = 0; i < nS; ++i) f32[i] = (float)m->host.Sf[i];
+  up(m->d_Sf32, f32.data(), nS * sizeof(float));
+  for (size_t i = 0; i < nP; ++i) f32[i] = (float)invJ[i];
+  up(m->d_invJ32, f32.data(), nP * sizeof(float));
+  for (size_t i = 0; i < 3 * nP; ++i) f32[i] = (float)m->host.x[i];
+  up(m->d_x32, f32.data(), 3 * nP * sizeof(float));
+  if (ce == cudaSuccess) ce = cudaMemsetAsync(m->d_err, 0, 4 * sizeof(unsigned), st);
+  if (ce == cudaSuccess) ce = cudaStreamSynchronize(st);
+  if (ce != cudaSuccess) {
+    free_mesh(m);
+    return CHORUS_ECUDA;
+  }
+  // the host keeps only what chorus_mesh_info needs
+  m->host.Sf.clear();
+  m->host.Sf.shrink_to_fit();
+  *out = m;
+  return CHORUS_OK;
+}
+
+chorus_status chorus_mesh_destroy(chorus_mesh m) {
+  if (!m) return CHORUS_EINVAL;
+  cudaDeviceSynchronize();
+  free_mesh(m);
+  return CHORUS_OK;
+}
+
+chorus_status chorus_mesh_info(chorus_mesh m, int64_t* n_dof, int64_t* n_faces, double* h_min, double* volume) {
+  if (!m) return CHORUS_EINVAL;
+  if (n_dof) *n_dof = m->E * m->N * m->N * m->N;
+  if (n_faces) *n_faces = m->host.n_interior_faces + m->host.n_wall_faces;
+  if (h_min) *h_min = m->host.h_min;
+  if (volume) *volume = m->host.volume;
+  return CHORUS_OK;
+}
+
+size_t chorus_rk_workspace_bytes(chorus_mesh m, chorus_precision prec) {
+  if (!m) return 0;
+  return ws_words(m) * (prec == CHORUS_FP64 ? sizeof(double) : sizeof(float)) + 256;
+}
+
+chorus_status chorus_prepare(chorus_mesh m, const chorus_params* P, void* stream) {
+  if (!m || !params_ok(P)) return CHORUS_EINVAL;
+  if (m->prepared && same_params(m->prep, *P)) return CHORUS_OK;
+  free_background(m);
+  cudaStream_t st = (cudaStream_t)stream;
+  const int N = m->N, N2 = N * N, N3 = N2 * N;
+  const size_t E = m->E, nP = E * N3, nT = E * 6 * 5 * N2;
+  if (dev_alloc(&m->d_Q0, 5 * nP) || dev_alloc(&m->d_bg, 2 * nP) || dev_alloc(&m->d_grho0, 3 * nP) ||
+      dev_alloc(&m->d_bgT, E * 6 * 2 * N2) || dev_alloc(&m->d_R0, 5 * nP)) {
+    free_background(m);
+    return CHORUS_ENOMEM;
+  }
+  double *T = nullptr, *Tv = nullptr, *R0 = nullptr, *gr = nullptr;
+  if (dev_alloc(&T, nT) || dev_alloc(&Tv, E * 6 * 4 * N2) || dev_alloc(&R0, 5 * nP) || dev_alloc(&gr, 3 * nP)) {
+    dev_free(T); dev_free(Tv); dev_free(R0); dev_free(gr);
+    free_background(m);
+    return CHORUS_ENOMEM;
+  }
+  const PhysArg<double> ph = phys_arg<double>(*P, m->r_inner, m->r_outer);
+  const MeshArg<double> ma = mesh_arg<double>(m);
+  cudaError_t ce = cudaSuccess;
+  k_background<<<grid1(nP), 256, 0, st>>>((int64_t)nP, N3, m->d_x64, ph, m->d_Q0);
+  ce = cudaGetLastError();
+  if (ce == cudaSuccess) ce = m->L.trace64(ma, m->ops64, m->d_Q0, T, st);
+  if (ce == cudaSuccess) ce = m->L.grad64(ma, m->ops64, ph, m->d_Q0, T, Tv, gr, m->d_err, st);
+  if (ce == cudaSuccess)
+    ce = m->L.resid64(ma, m->ops64, ph, m->d_Q0, T, Tv, R0, nullptr, nullptr, 0.0, 1.0, 0.0, kModeResidual, m->d_err, st);
+  if (ce == cudaSuccess) {
+    k_d2f<<<grid1(5 * nP), 256, 0, st>>>((int64_t)(5 * nP), R0, m->d_R0);
+    k_d2f<<<grid1(3 * nP), 256, 0, st>>>((int64_t)(3 * nP), gr, m->d_grho0);
+    k_bg_tables<<<grid1(std::max(nP, E * 6 * N2)), 256, 0, st>>>((int64_t)E, N3, N2, m->d_Q0, T, m->d_bg, m->d_bgT);
+    ce = cudaGetLastError();
+  }
+  if (ce == cudaSuccess) ce = cudaStreamSynchronize(st);
+  dev_free(T); dev_free(Tv); dev_free(R0); dev_free(gr);
+  if (ce != cudaSuccess) {
+    free_background(m);
+    return CHORUS_ECUDA;
+  }
+  m->prep = *P;
+  m->prepared = true;
+  return CHORUS_OK;
+}
+
+chorus_status chorus_state_init(chorus_mesh m, const chorus_params* P, uint64_t seed, double amp,
+                                chorus_precision prec, void* Q, void* stream) {
+  if (!m || !Q || !params_ok(P) || !(amp >= 0.0 && amp < 1.0) || (prec != CHORUS_FP64 && prec != CHORUS_FP32_PERT))
+    return CHORUS_EINVAL;
+  chorus_status s = chorus_prepare(m, P, stream);
+  if (s != CHORUS_OK) return s;
+  const int64_t nP = m->E * m->N * m->N * m->N;
+  cudaStream_t st = (cudaStream_t)stream;
+  k_init<<<grid1(nP), 256, 0, st>>>(nP, m->N * m->N * m->N, m->d_Q0, seed, amp, prec == CHORUS_FP32_PERT,
+                                     (double*)Q, (float*)Q);
+  return cu(cudaGetLastError());
+}
+
+chorus_status chorus_residual(chorus_mesh m, const chorus_params* P, chorus_precision prec, const void* Q, void* R,
+                              void* workspace, void* stream) {
+  if (!m || !Q || !R || !workspace || !params_ok(P)) return CHORUS_EINVAL;
+  cudaStream_t st = (cudaStream_t)stream;
+  if (prec == CHORUS_FP64) {
+    const PhysArg<double> ph = phys_arg<double>(*P, m->r_inner, m->r_outer);
+    const MeshArg<double> ma = mesh_arg<double>(m);
+    Ws<double> w = split_ws<double>(m, workspace);
+    CHK(timed(m, 0, st, [&] { return m->L.trace64(ma, m->ops64, (const double*)Q, w.Ta, st); }));
+    CHK(timed(m, 1, st, [&] { return m->L.grad64(ma, m->ops64, ph, (const double*)Q, w.Ta, w.Tv, nullptr, m->d_err, st); }));
+    CHK(timed(m, 2, st, [&] {
+      return m->L.resid64(ma, m->ops64, ph, (const double*)Q, w.Ta, w.Tv, (double*)R, nullptr, nullptr, 0.0, 1.0, 0.0,
+                          kModeResidual, m->d_err, st);
+    }));
+    return CHORUS_OK;
+  }
+  if (prec != CHORUS_FP32_PERT) return CHORUS_EINVAL;
+  if (!m->prepared || !same_params(m->prep, *P)) return CHORUS_EINVAL;
+  const PhysArg<float> ph = phys_arg<float>(*P, m->r_inner, m->r_outer);
+  const MeshArg<float> ma = mesh_arg<float>(m);
+  Ws<float> w = split_ws<float>(m, workspace);
+  const BgArg bg = bg_arg(m);
+  CHK(timed(m, 0, st, [&] { return m->L.trace32(ma, m->ops32, (const float*)Q, w.Ta, st); }));
+  CHK(timed(m, 1, st, [&] { return m->L.grad32(ma, m->ops32, ph, bg, (const float*)Q, w.Ta, w.Tv, m->d_err, st); }));
+  CHK(timed(m, 2, st, [&] {
+    return m->L.resid32(ma, m->ops32, ph, bg, (const float*)Q, w.Ta, w.Tv, (float*)R, nullptr, nullptr, 0.0f, 1.0f,
+                        0.0f, kModeResidual, m->d_err, st);
+  }));
+  return CHORUS_OK;
+}
+
+chorus_status chorus_rk_step(chorus_mesh m, const chorus_params* P, chorus_precision prec, void* Q, void* workspace,
+                             double dt, int64_t n_steps, void* stream) {
+  if (!m || !Q || !workspace || !params_ok(P) || !(dt > 0.0) || !std::isfinite(dt) || n_steps < 0) return CHORUS_EINVAL;
+  if (n_steps == 0) return CHORUS_OK;
+  cudaStream_t st = (cudaStream_t)stream;
+  static const double ca[3] = {0.0, 0.75, 1.0 / 3.0};
+  static const double cb[3] = {1.0, 0.25, 2.0 / 3.0};
+  if (prec == CHORUS_FP64) {
+    const PhysArg<double> ph = phys_arg<double>(*P, m->r_inner, m->r_outer);
+    const MeshArg<double> ma = mesh_arg<double>(m);
+    Ws<double> w = split_ws<double>(m, workspace);
+    double* u = (double*)Q;
+    double *Tc = w.Ta, *Tn = w.Tb;
+    CHK(timed(m, 0, st, [&] { return m->L.trace64(ma, m->ops64, u, Tc, st); }));
+    for (int64_t n = 0; n < n_steps; ++n)
+      for (int k = 0; k < 3; ++k) {
+        const double* src = k == 0 ? u : w.s;
+        double* dst = k == 2 ? u : w.s;
+        CHK(timed(m, 1, st, [&] { return m->L.grad64(ma, m->ops64, ph, src, Tc, w.Tv, nullptr, m->d_err, st); }));
+        CHK(timed(m, 2, st, [&] {
+          return m->L.resid64(ma, m->ops64, ph, src, Tc, w.Tv, dst, Tn, u, ca[k], cb[k], dt, kModeRK, m->d_err, st);
+        }));
+        std::swap(Tc, Tn);
+      }
+    return CHORUS_OK;
+  }
+  if (prec != CHORUS_FP32_PERT) return CHORUS_EINVAL;
+  if (!m->prepared || !same_params(m->prep, *P)) return CHORUS_EINVAL;
+  const PhysArg<float> ph = phys_arg<float>(*P, m->r_inner, m->r_outer);
+  const MeshArg<float> ma = mesh_arg<float>(m);
+  const BgArg bg = bg_arg(m);
+  Ws<float> w = split_ws<float>(m, workspace);
+  float* u = (float*)Q;
+  float *Tc = w.Ta, *Tn = w.Tb;
+  CHK(timed(m, 0, st, [&] { return m->L.trace32(ma, m->ops32, u, Tc, st); }));
+  for (int64_t n = 0; n < n_steps; ++n)
+    for (int k = 0; k < 3; ++k) {
+      const float* src = k == 0 ? u : w.s;
+      float* dst = k == 2 ? u : w.s;
+      CHK(timed(m, 1, st, [&] { return m->L.grad32(ma, m->ops32, ph, bg, src, Tc, w.Tv, m->d_err, st); }));
+      CHK(timed(m, 2, st, [&] {
+        return m->L.resid32(ma, m->ops32, ph, bg, src, Tc, w.Tv, dst, Tn, u, (float)ca[k], (float)cb[k], (float)dt,
+                            kModeRK, m->d_err, st);
+      }));
+      std::swap(Tc, Tn);
+    }
+  return CHORUS_OK;
+}
+
+chorus_status chorus_reduce(chorus_mesh m, const chorus_params* P, chorus_precision prec, const void* Q, double* out,
+                            void* stream) {
+  if (!m || !Q || !out) return CHORUS_EINVAL;
+  cudaStream_t st = (cudaStream_t)stream;
+  const int N3 = m->N * m->N * m->N;
+  const int64_t nP = m->E * N3;
+  if (prec == CHORUS_FP64) {
+    k_reduce_partial<double><<<kRedBlocks, 256, 0, st>>>(nP, N3, (const double*)Q, nullptr, m->d_wJ, m->d_x64, m->d_red);
+  } else if (prec == CHORUS_FP32_PERT) {
+    if (!P || !m->prepared || !same_params(m->prep, *P)) return CHORUS_EINVAL;
+    k_reduce_partial<float><<<kRedBlocks, 256, 0, st>>>(nP, N3, (const float*)Q, m->d_Q0, m->d_wJ, m->d_x64, m->d_red);
+  } else {
+    return CHORUS_EINVAL;
+  }
+  k_reduce_final<<<1, 32, 0, st>>>(kRedBlocks, m->d_red, m->d_red + kRedBlocks * 6);
+  CHK(cudaGetLastError());
+  double r[6];
+  CHK(cudaMemcpyAsync(r, m->d_red + kRedBlocks * 6, sizeof(r), cudaMemcpyDeviceToHost, st));
+  CHK(cudaStreamSynchronize(st));
+  out[0] = r[0];
+  out[1] = r[1];
+  out[2] = r[2];
+  out[3] = std::sqrt(r[3] * r[3] + r[4] * r[4] + r[5] * r[5]);
+  for (int i = 0; i < 4; ++i)
+    if (!std::isfinite(out[i])) return CHORUS_ENAN;
+  unsigned err = 0;
+  CHK(cudaMemcpy(&err, m->d_err, sizeof(unsigned), cudaMemcpyDeviceToHost));
+  return err ? CHORUS_ETIMEOUT : CHORUS_OK;
+}
+
+chorus_status chorus_timing_enable(chorus_mesh m, int enable) {
+  if (!m) return CHORUS_EINVAL;
+  m->timing = enable != 0;
+  return CHORUS_OK;
+}
+
+chorus_status chorus_timing_read(chorus_mesh m, void* stream, double* ms, int64_t* counts) {
+  if (!m || !ms || !counts) return CHORUS_EINVAL;
+  CHK(cudaStreamSynchronize((cudaStream_t)stream));
+  for (int c = 0; c < 3; ++c) {
+    ms[c] = 0.0;
+    counts[c] = 0;
+  }
+  cudaError_t e = cudaSuccess;
+  for (auto& r : m->recs) {
+    float t = 0.f;
+    if (e == cudaSuccess) e = cudaEventElapsedTime(&t, r.a, r.b);
+    if (r.cls >= 0 && r.cls < 3) {
+      ms[r.cls] += t;
+      counts[r.cls] += 1;
+    }
+  }
+  release_records(m);
+  return cu(e);
+}
+
+chorus_status chorus_check(chorus_mesh m, void* stream) {
+  if (!m) return CHORUS_EINVAL;
+  CHK(cudaStreamSynchronize((cudaStream_t)stream));
+  unsigned err = 0;
+  CHK(cudaMemcpy(&err, m->d_err, sizeof(unsigned), cudaMemcpyDeviceToHost));
+  return err ? CHORUS_ETIMEOUT : CHORUS_OK;
+}
+
+}  // extern "C"

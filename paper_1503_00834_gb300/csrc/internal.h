@@ -1,0 +1,73 @@
+// Internal structures shared by the C-ABI layer and the per-order kernel translation units.
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace chorus {
+
+constexpr int kMaxN = 6;
+
+// 1D operators for one order, passed to kernels by value (parameter bank).
+template <class R>
+struct OpsArg {
+  R I[kMaxN + 1][kMaxN];     // h_s(Xf_f)
+  R D[kMaxN][kMaxN + 1];     // l'_f(X_s)
+  R Dsol[kMaxN][kMaxN];      // D I
+  R Lfs[kMaxN][kMaxN + 1];   // l_a(X_s)
+  R w[kMaxN];                // quadrature weights
+};
+
+// Physical constants derived from chorus_params (nondimensional).
+template <class R>
+struct PhysArg {
+  R gamma, gm1, Rgas, CpR;   // CpR = C_p / R_gas
+  R kappa, kappa_r, nu;
+  R GM, twoOmega;
+  R T_top, bottom_flux;
+  // polytrope (Eqs. 25-27): chi = c + alpha d / r, rho_a = rho_c chi^n, p_a = p_c chi^(n+1)
+  double chi_c, chi_ad, rho_c, p_c, poly_n;
+};
+
+// Mesh data on the device for one precision.
+template <class R>
+struct MeshArg {
+  int E;
+  const int* nbr;    // [E][6] neighbour element, -1 inner wall, -2 outer wall
+  const int* code;   // [E][6] neighbour local face * 8 + orientation bits
+  const R* Sf;       // [E][3 d][3 n][N+1 f][N*N line]  S^d_n = |J| d xi_d / d x_n at the d-flux points
+  const R* invJ;     // [E][N^3] 1/|J| at the solution points
+  const R* x;        // [E][3][N^3] solution-point coordinates
+};
+
+// Background tables of the perturbation path (float, from FP64 computations).
+struct BgArg {
+  const float* bg;     // [E][2][N^3]     rho0, E0
+  const float* grho0;  // [E][3][N^3]     lifted background density gradient
+  const float* bgT;    // [E][6][2][N^2]  rho0, E0 on the face points
+  const float* R0;     // [E][5][N^3]     FP64 residual of the background, rounded
+};
+
+enum ResidMode { kModeResidual = 0, kModeRK = 1 };
+
+// Per-order launchers (defined in kern_p<N>.cu).  All return cudaGetLastError().
+struct LaunchSet {
+  cudaError_t (*trace64)(const MeshArg<double>&, const OpsArg<double>&, const double* q, double* T, cudaStream_t);
+  cudaError_t (*grad64)(const MeshArg<double>&, const OpsArg<double>&, const PhysArg<double>&, const double* q,
+                        const double* T, double* Tv, double* grad_rho_out, unsigned* err, cudaStream_t);
+  cudaError_t (*resid64)(const MeshArg<double>&, const OpsArg<double>&, const PhysArg<double>&, const double* q,
+                         const double* T, const double* Tv, double* out, double* T_out, const double* un,
+                         double a, double b, double dt, int mode, unsigned* err, cudaStream_t);
+  cudaError_t (*trace32)(const MeshArg<float>&, const OpsArg<float>&, const float* q, float* T, cudaStream_t);
+  cudaError_t (*grad32)(const MeshArg<float>&, const OpsArg<float>&, const PhysArg<float>&, const BgArg&,
+                        const float* q, const float* T, float* Tv, unsigned* err, cudaStream_t);
+  cudaError_t (*resid32)(const MeshArg<float>&, const OpsArg<float>&, const PhysArg<float>&, const BgArg&,
+                         const float* q, const float* T, const float* Tv, float* out, float* T_out,
+                         const float* un, float a, float b, float dt, int mode, unsigned* err, cudaStream_t);
+};
+
+LaunchSet launchers_p2();
+LaunchSet launchers_p3();
+LaunchSet launchers_p4();
+LaunchSet launchers_p5();
+
+}  // namespace chorus

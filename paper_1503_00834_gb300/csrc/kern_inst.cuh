@@ -1,0 +1,56 @@
+// Launchers of the residual kernels for one order N, for the FP64 total-state form and the FP32
+// perturbation form.  Each kern_p<p>.cu instantiates this header once.
+#pragma once
+#include "sd_kernels.cuh"
+
+namespace chorus {
+
+template <int N, int EPB64, int EPB32>
+struct Inst {
+  using L64 = Launch<N, false, double, EPB64>;
+  using L32 = Launch<N, true, float, EPB32>;
+
+  static cudaError_t trace64(const MeshArg<double>& m, const OpsArg<double>& ops, const double* q, double* T,
+                             cudaStream_t st) {
+    return L64::trace(m, ops, q, T, st);
+  }
+  static cudaError_t trace32(const MeshArg<float>& m, const OpsArg<float>& ops, const float* q, float* T,
+                             cudaStream_t st) {
+    return L32::trace(m, ops, q, T, st);
+  }
+  static cudaError_t grad64(const MeshArg<double>& m, const OpsArg<double>& ops, const PhysArg<double>& ph,
+                            const double* q, const double* T, double* Tv, double* grad_rho_out, unsigned* err,
+                            cudaStream_t st) {
+    KArgs<double> A{};
+    A.m = m; A.ops = ops; A.ph = ph; A.q = q; A.T = T; A.Tv_out = Tv; A.grad_rho_out = grad_rho_out; A.err = err;
+    return L64::grad(A, st);
+  }
+  static cudaError_t grad32(const MeshArg<float>& m, const OpsArg<float>& ops, const PhysArg<float>& ph,
+                            const BgArg& bg, const float* q, const float* T, float* Tv, unsigned* err,
+                            cudaStream_t st) {
+    KArgs<float> A{};
+    A.m = m; A.ops = ops; A.ph = ph; A.bg = bg; A.q = q; A.T = T; A.Tv_out = Tv; A.err = err;
+    return L32::grad(A, st);
+  }
+  static cudaError_t resid64(const MeshArg<double>& m, const OpsArg<double>& ops, const PhysArg<double>& ph,
+                             const double* q, const double* T, const double* Tv, double* out, double* T_out,
+                             const double* un, double a, double b, double dt, int mode, unsigned* err,
+                             cudaStream_t st) {
+    KArgs<double> A{};
+    A.m = m; A.ops = ops; A.ph = ph; A.q = q; A.T = T; A.Tv = Tv; A.out = out; A.T_out = T_out; A.un = un;
+    A.a = a; A.b = b; A.dt = dt; A.err = err;
+    return mode == kModeRK ? L64::template resid<kModeRK>(A, st) : L64::template resid<kModeResidual>(A, st);
+  }
+  static cudaError_t resid32(const MeshArg<float>& m, const OpsArg<float>& ops, const PhysArg<float>& ph,
+                             const BgArg& bg, const float* q, const float* T, const float* Tv, float* out,
+                             float* T_out, const float* un, float a, float b, float dt, int mode, unsigned* err,
+                             cudaStream_t st) {
+    KArgs<float> A{};
+    A.m = m; A.ops = ops; A.ph = ph; A.bg = bg; A.q = q; A.T = T; A.Tv = Tv; A.out = out; A.T_out = T_out;
+    A.un = un; A.a = a; A.b = b; A.dt = dt; A.err = err;
+    return mode == kModeRK ? L32::template resid<kModeRK>(A, st) : L32::template resid<kModeResidual>(A, st);
+  }
+  static LaunchSet set() { return LaunchSet{trace64, grad64, resid64, trace32, grad32, resid32}; }
+};
+
+}  // namespace chorus

@@ -1,0 +1,8 @@
+// Residual kernels of order p = 3 (N = 4 solution points per direction).
+// Elements per CTA: 4 (FP64 form), 8 (FP32 perturbation form); chosen so that a CTA's state block
+// is a multiple of 16 bytes (bulk-copy granularity) and the CTA stays near 128 threads.
+#include "kern_inst.cuh"
+
+namespace chorus {
+LaunchSet launchers_p3() { return Inst<4, 4, 8>::set(); }
+}  // namespace chorus

@@ -1,0 +1,8 @@
+// Residual kernels of order p = 5 (N = 6 solution points per direction).
+// Elements per CTA: 2 (FP64 form), 4 (FP32 perturbation form); chosen so that a CTA's state block
+// is a multiple of 16 bytes (bulk-copy granularity) and the CTA stays near 128 threads.
+#include "kern_inst.cuh"
+
+namespace chorus {
+LaunchSet launchers_p5() { return Inst<6, 2, 4>::set(); }
+}  // namespace chorus

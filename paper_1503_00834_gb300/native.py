@@ -1,0 +1,198 @@
+"""ctypes binding of libchorus.so (the C ABI declared in include/chorus.h).
+
+Argument marshalling only: every step of the residual and the time stepping runs in the library's
+CUDA kernels.  Device buffers are torch tensors (contiguous, on the current CUDA device); the
+stream is torch's current stream unless one is given.  There is no CPU fallback: if the library is
+missing the calls raise.
+"""
+from __future__ import annotations
+
+import ctypes
+import math
+import os
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libchorus.so")
+
+FP64 = 0
+FP32_PERT = 1
+
+STATUS = {0: "ok", 1: "invalid argument", 2: "out of memory", 3: "CUDA error", 4: "invalid mesh",
+          5: "non-finite value", 6: "device wait timed out", 7: "unsupported"}
+
+# every symbol declared in include/chorus.h
+EXPORTS = ("chorus_mesh_create", "chorus_mesh_destroy", "chorus_mesh_info", "chorus_prepare", "chorus_state_init",
+           "chorus_residual", "chorus_rk_workspace_bytes", "chorus_rk_step", "chorus_reduce", "chorus_check",
+           "chorus_strerror", "chorus_timing_enable", "chorus_timing_read")
+
+
+class ChorusError(RuntimeError):
+    def __init__(self, call: str, status: int):
+        super().__init__(f"{call}: {STATUS.get(status, status)} (status {status})")
+        self.status = status
+
+
+class Params(ctypes.Structure):
+    """chorus_params (all doubles, in header order)."""
+
+    _fields_ = [(n, ctypes.c_double) for n in ("gamma", "R_gas", "GM", "Omega", "nu", "kappa", "kappa_r", "poly_n",
+                                                "N_rho", "rho_c", "bottom_flux", "T_top")]
+
+    @classmethod
+    def from_phys(cls, phys) -> "Params":
+        return cls(*phys.as_tuple())
+
+
+_lib = None
+
+
+def load() -> ctypes.CDLL:
+    """Load libchorus.so; raises if it has not been built."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(LIB_PATH):
+        raise RuntimeError(f"{LIB_PATH} is missing: build it with `python -m paper_1503_00834_gb300.build`")
+    lib = ctypes.CDLL(LIB_PATH)
+    vp, i64, f64, i32 = ctypes.c_void_p, ctypes.c_int64, ctypes.c_double, ctypes.c_int
+    P = ctypes.POINTER
+    sig = {
+        "chorus_mesh_create": (i32, [i64, P(f64), i64, P(i64), i32, f64, f64, i32, vp, P(vp)]),
+        "chorus_mesh_destroy": (i32, [vp]),
+        "chorus_mesh_info": (i32, [vp, P(i64), P(i64), P(f64), P(f64)]),
+        "chorus_prepare": (i32, [vp, P(Params), vp]),
+        "chorus_state_init": (i32, [vp, P(Params), ctypes.c_uint64, f64, i32, vp, vp]),
+        "chorus_residual": (i32, [vp, P(Params), i32, vp, vp, vp, vp]),
+        "chorus_rk_workspace_bytes": (ctypes.c_size_t, [vp, i32]),
+        "chorus_rk_step": (i32, [vp, P(Params), i32, vp, vp, f64, i64, vp]),
+        "chorus_reduce": (i32, [vp, P(Params), i32, vp, P(f64), vp]),
+        "chorus_check": (i32, [vp, vp]),
+        "chorus_strerror": (ctypes.c_char_p, [i32]),
+        "chorus_timing_enable": (i32, [vp, i32]),
+        "chorus_timing_read": (i32, [vp, vp, P(f64), P(i64)]),
+    }
+    for name, (res, args) in sig.items():
+        fn = getattr(lib, name)
+        fn.restype = res
+        fn.argtypes = args
+    _lib = lib
+    return lib
+
+
+def _ok(call: str, status: int) -> None:
+    if status != 0:
+        raise ChorusError(call, status)
+
+
+def _stream(stream):
+    if stream is None:
+        import torch
+
+        return ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
+    return ctypes.c_void_p(int(stream))
+
+
+def _ptr(t) -> ctypes.c_void_p:
+    if not t.is_cuda or not t.is_contiguous():
+        raise ValueError("expected a contiguous CUDA tensor")
+    return ctypes.c_void_p(t.data_ptr())
+
+
+class Mesh:
+    """A curved hexahedral shell mesh on the GPU (chorus_mesh handle)."""
+
+    def __init__(self, node_xyz: np.ndarray, hex20: np.ndarray, p: int, r_inner: float, r_outer: float,
+                 metric_mode: int = 0, stream=None):
+        lib = load()
+        xyz = np.ascontiguousarray(node_xyz, dtype=np.float64)
+        h20 = np.ascontiguousarray(hex20, dtype=np.int64)
+        self.p, self.N = p, p + 1
+        self.n_elem = h20.shape[0]
+        handle = ctypes.c_void_p()
+        _ok("chorus_mesh_create", lib.chorus_mesh_create(
+            xyz.shape[0], xyz.ctypes.data_as(ctypes.POINTER(ctypes.c_double)), h20.shape[0],
+            h20.ctypes.data_as(ctypes.POINTER(ctypes.c_int64)), p, r_inner, r_outer, metric_mode, _stream(stream),
+            ctypes.byref(handle)))
+        self.handle = handle
+
+    def close(self) -> None:
+        if getattr(self, "handle", None) and self.handle.value:
+            load().chorus_mesh_destroy(self.handle)
+            self.handle = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def info(self) -> dict:
+        n_dof, n_faces = ctypes.c_int64(), ctypes.c_int64()
+        h_min, vol = ctypes.c_double(), ctypes.c_double()
+        _ok("chorus_mesh_info", load().chorus_mesh_info(self.handle, ctypes.byref(n_dof), ctypes.byref(n_faces),
+                                                        ctypes.byref(h_min), ctypes.byref(vol)))
+        return dict(n_dof=n_dof.value, n_faces=n_faces.value, h_min=h_min.value, volume=vol.value)
+
+    def state_shape(self):
+        return (self.n_elem, 5, self.N ** 3)
+
+    def prepare(self, params: Params, stream=None) -> None:
+        _ok("chorus_prepare", load().chorus_prepare(self.handle, ctypes.byref(params), _stream(stream)))
+
+    def workspace_bytes(self, prec: int) -> int:
+        return int(load().chorus_rk_workspace_bytes(self.handle, prec))
+
+    def state_init(self, params: Params, seed: int, amp: float, prec: int, Q, stream=None) -> None:
+        _ok("chorus_state_init", load().chorus_state_init(self.handle, ctypes.byref(params), seed, amp, prec, _ptr(Q),
+                                                          _stream(stream)))
+
+    def residual(self, params: Params, prec: int, Q, R, ws, stream=None) -> None:
+        _ok("chorus_residual", load().chorus_residual(self.handle, ctypes.byref(params), prec, _ptr(Q), _ptr(R),
+                                                      _ptr(ws), _stream(stream)))
+
+    def rk_step(self, params: Params, prec: int, Q, ws, dt: float, n_steps: int, stream=None) -> None:
+        _ok("chorus_rk_step", load().chorus_rk_step(self.handle, ctypes.byref(params), prec, _ptr(Q), _ptr(ws), dt,
+                                                    n_steps, _stream(stream)))
+
+    def reduce(self, params: Params, prec: int, Q, stream=None) -> np.ndarray:
+        out = (ctypes.c_double * 4)()
+        _ok("chorus_reduce", load().chorus_reduce(self.handle, ctypes.byref(params), prec, _ptr(Q), out,
+                                                  _stream(stream)))
+        return np.array(out[:])
+
+    def timing_enable(self, enable: bool) -> None:
+        _ok("chorus_timing_enable", load().chorus_timing_enable(self.handle, 1 if enable else 0))
+
+    def timing_read(self, stream=None):
+        """(ms[3], counts[3]) per kernel class: 0 traces, 1 gradients, 2 residual/RK update."""
+        ms = (ctypes.c_double * 3)()
+        cnt = (ctypes.c_int64 * 3)()
+        _ok("chorus_timing_read", load().chorus_timing_read(self.handle, _stream(stream), ms, cnt))
+        return list(ms), list(cnt)
+
+    def check(self, stream=None) -> None:
+        _ok("chorus_check", load().chorus_check(self.handle, _stream(stream)))
+
+
+def stable_dt(p: int, h_min: float, wave_speed: float, diffusivity: float) -> float:
+    """Fixed explicit step: 0.5 h/((2p+1) max(|u|+c)), capped by 0.25 h^2/((2p+1)^2 max(nu, kappa))."""
+    dt = 0.5 * h_min / ((2 * p + 1) * wave_speed)
+    if diffusivity > 0:
+        dt = min(dt, 0.25 * h_min * h_min / ((2 * p + 1) ** 2 * diffusivity))
+    return dt
+
+
+def max_sound_speed(phys, r_inner: float, r_outer: float) -> float:
+    """Largest sound speed of the polytrope at rest (at the inner wall, where T is highest)."""
+    beta = r_inner / r_outer
+    d = r_outer - r_inner
+    n = phys.poly_n
+    chi_o = (beta + 1.0) / (beta * math.exp(phys.N_rho / n) + 1.0)
+    c = (2.0 * chi_o - beta - 1.0) / (1.0 - beta)
+    alpha = (1.0 + beta) * (1.0 - chi_o) / (1.0 - beta) ** 2
+    p_c = phys.GM * phys.rho_c / ((n + 1.0) * alpha * d)
+    T_c = p_c / (phys.R_gas * phys.rho_c)
+    chi_i = c + alpha * d / r_inner
+    return math.sqrt(phys.gamma * phys.R_gas * T_c * chi_i)

@@ -1,0 +1,206 @@
+"""GPU parity: the CUDA path through the C ABI against the FP64 CPU oracle.
+
+Tolerances (see the module docstring of gpu_common for the norm):
+  * FP64 residual: 1e-12 relative *backward* error.  The residual of a near-hydrostatic state is a
+    difference of O(rho g) terms that cancel to the perturbation level, so its relative forward
+    error is its condition number times the backward error.  The test measures the condition
+    number kappa_v of each variable on the oracle (relative change of R_v under a random relative
+    input change of 1e-10, divided by 1e-10) and requires e_v <= 1e-12 * max(1, kappa_v).
+  * FP64 states after RK steps: the oracle trajectory is re-run with a relative 2^-53 random
+    perturbation of the state after every stage (a model of FP64 storage rounding); the spread of
+    the two oracle runs is the trajectory's own rounding noise, and the GPU must agree with the
+    oracle to max(1e-12, 10 x that spread).
+  * FP32 perturbation path: 1e-5 relative L2 for the residual and for q' after steps.
+"""
+import numpy as np
+import pytest
+
+from chorus_inputs import SHELL_288_P3, small_shell
+from gpu_common import OracleShell, rel_err, to5
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _built():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1503_00834_gb300 import build
+
+    build.build()
+
+
+def _gpu(cfg):
+    from paper_1503_00834_gb300 import Shell
+
+    return Shell(cfg)
+
+
+def _alloc(mesh, prec, n=1):
+    dt = torch.float64 if prec == 0 else torch.float32
+    return [torch.empty(mesh.state_shape(), dtype=dt, device="cuda") for _ in range(n)]
+
+
+def _ws(mesh, prec):
+    return torch.empty(mesh.workspace_bytes(prec), dtype=torch.uint8, device="cuda")
+
+
+def _condition(osh, Q, R_ref, W, delta=1e-10):
+    """Per-variable condition number of the oracle residual under a random relative input change."""
+    from oracle.residual import residual
+
+    rng = np.random.default_rng(123)
+    Qp = Q * (1.0 + delta * rng.uniform(-1.0, 1.0, Q.shape))
+    _, rel = rel_err(residual(osh.disc, osh.ph, Qp), R_ref, W)
+    return rel / delta
+
+
+# the one-element-thick shell uses a mild stratification so that its traces stay positive
+CASES = [SHELL_288_P3, small_shell(2, 2, 2), small_shell(2, 2, 4), small_shell(1, 2, 5),
+         small_shell(1, 1, 3, N_rho=0.5)]
+
+
+@pytest.mark.parametrize("cfg", CASES, ids=lambda c: c.name)
+def test_initial_state_matches_oracle(cfg):
+    from paper_1503_00834_gb300 import FP32_PERT, FP64
+
+    sh = _gpu(cfg)
+    osh = OracleShell(cfg)
+    Q64, q32 = _alloc(sh.mesh, FP64)[0], _alloc(sh.mesh, FP32_PERT)[0]
+    sh.mesh.state_init(sh.params, cfg.seed, cfg.entropy_amp, FP64, Q64)
+    sh.mesh.state_init(sh.params, cfg.seed, cfg.entropy_amp, FP32_PERT, q32)
+    torch.cuda.synchronize()
+    Qref = osh.initial_state()
+    N = cfg.p + 1
+    W = osh.weights()
+    assert np.max(np.abs(to5(Q64, N) - Qref)) <= 1e-14 * np.max(np.abs(Qref))
+    Q0 = osh.background()
+    e, _ = rel_err(to5(q32, N), Qref - Q0, W)
+    assert e < 1e-6  # FP32 rounding of the perturbation
+
+
+@pytest.mark.parametrize("cfg", CASES, ids=lambda c: c.name)
+def test_residual_fp64_and_fp32_match_oracle(cfg):
+    from oracle.residual import residual
+    from paper_1503_00834_gb300 import FP32_PERT, FP64
+
+    sh = _gpu(cfg)
+    osh = OracleShell(cfg)
+    N = cfg.p + 1
+    Q64, R64 = _alloc(sh.mesh, FP64, 2)
+    q32, R32 = _alloc(sh.mesh, FP32_PERT, 2)
+    sh.mesh.state_init(sh.params, cfg.seed, cfg.entropy_amp, FP64, Q64)
+    sh.mesh.state_init(sh.params, cfg.seed, cfg.entropy_amp, FP32_PERT, q32)
+    sh.mesh.residual(sh.params, FP64, Q64, R64, _ws(sh.mesh, FP64))
+    sh.mesh.residual(sh.params, FP32_PERT, q32, R32, _ws(sh.mesh, FP32_PERT))
+    sh.mesh.check()
+    Q = osh.initial_state()
+    Rref = residual(osh.disc, osh.ph, Q)
+    W = osh.weights()
+    _, e64 = rel_err(to5(R64, N), Rref, W)
+    kappa = _condition(osh, Q, Rref, W)
+    print(f"{cfg.name}: FP64 residual rel err {e64}, condition {kappa}")
+    assert np.all(e64 <= 1e-12 * np.maximum(1.0, kappa))
+    e32, ev = rel_err(to5(R32, N), Rref, W)
+    print(f"{cfg.name}: FP32 residual rel err {ev}")
+    assert e32 < 1e-5
+
+
+@pytest.mark.parametrize("prec", [0, 1], ids=["fp64", "fp32pert"])
+def test_rk_steps_match_oracle(prec):
+    """The 288-element p=3 shell advanced by SSP-RK3 on both sides; compared on q' = Q - Q0."""
+    from oracle import rk
+    from paper_1503_00834_gb300 import FP64
+
+    cfg = SHELL_288_P3
+    n_steps = 100 if prec == FP64 else 20
+    sh = _gpu(cfg)
+    osh = OracleShell(cfg)
+    N = cfg.p + 1
+    Q = _alloc(sh.mesh, prec)[0]
+    sh.mesh.state_init(sh.params, cfg.seed, cfg.entropy_amp, prec, Q)
+    sh.mesh.rk_step(sh.params, prec, Q, _ws(sh.mesh, prec), sh.dt, n_steps)
+    sh.mesh.check()
+    Qinit = osh.initial_state()
+    Qref = rk.run(osh.disc, osh.ph, Qinit, sh.dt, n_steps)
+    Q0 = osh.background()
+    W = osh.weights()
+    got = to5(Q, N) - (Q0 if prec == FP64 else 0.0)
+    e, ev = rel_err(got, Qref - Q0, W)
+    print(f"rk {n_steps} steps prec {prec}: rel err on q' {ev}")
+    if prec == FP64:
+        noisy = _noisy_run(osh, Qinit, sh.dt, n_steps)
+        _, spread = rel_err(noisy - Q0, Qref - Q0, W)
+        print(f"oracle rounding spread {spread}")
+        assert np.all(ev <= np.maximum(1e-12, 10.0 * spread))
+    else:
+        assert e < 1e-5
+
+
+def _noisy_run(osh, Q, dt, n_steps):
+    """Oracle SSP-RK3 with a relative 2^-53 random perturbation of the state after every stage."""
+    from oracle.residual import residual
+    from oracle.rk import SSPRK3
+
+    rng = np.random.default_rng(7)
+    eps = 2.0 ** -53
+    u = Q * (1.0 + eps * rng.uniform(-1.0, 1.0, Q.shape))
+    for _ in range(n_steps):
+        s = u
+        for a, b in SSPRK3:
+            s = a * u + b * (s + dt * residual(osh.disc, osh.ph, s))
+            s = s * (1.0 + eps * rng.uniform(-1.0, 1.0, s.shape))
+        u = s
+    return u
+
+
+def test_reductions_match_oracle():
+    from oracle.diagnostics import integrals
+    from paper_1503_00834_gb300 import FP32_PERT, FP64
+
+    cfg = SHELL_288_P3
+    sh = _gpu(cfg)
+    osh = OracleShell(cfg)
+    Q64, q32 = _alloc(sh.mesh, FP64)[0], _alloc(sh.mesh, FP32_PERT)[0]
+    sh.mesh.state_init(sh.params, cfg.seed, cfg.entropy_amp, FP64, Q64)
+    sh.mesh.state_init(sh.params, cfg.seed, cfg.entropy_amp, FP32_PERT, q32)
+    Q = osh.initial_state()
+    ref = integrals(osh.disc, Q)
+    out64 = sh.mesh.reduce(sh.params, FP64, Q64)
+    out32 = sh.mesh.reduce(sh.params, FP32_PERT, q32)
+    for out, tol in ((out64, 1e-13), (out32, 1e-9)):
+        assert abs(out[0] - ref["mass"]) < tol * ref["mass"]
+        assert abs(out[1] - ref["energy"]) < tol * ref["energy"]
+        assert abs(out[2] - ref["kinetic"]) < 1e-30 + tol
+        assert abs(out[3] - np.linalg.norm(ref["L"])) < 1e-30 + tol
+    info = sh.mesh.info()
+    assert abs(info["volume"] - ref["volume"]) < 1e-13 * ref["volume"]
+    assert info["n_dof"] == cfg.n_dof and info["n_faces"] == 768 + 192
+
+
+def test_freestream_on_gpu():
+    """A uniform flow with no gravity or rotation stays uniform away from the walls (FP64 path)."""
+    import dataclasses
+
+    from chorus_inputs import ShellConfig
+    from paper_1503_00834_gb300 import FP64, Params, Shell
+
+    base = small_shell(2, 5, 3)
+    phys = dataclasses.replace(base.phys, GM=1e-30, Omega=0.0, nu=0.0, kappa=0.0)
+    cfg = ShellConfig(base.name, base.n, base.n_r, base.p, base.r_inner, base.r_outer, 1, 0.0, 1, phys)
+    sh = Shell(cfg)
+    N = cfg.p + 1
+    E = cfg.n_elem
+    rho, u, p, gam = 1.3, np.array([0.3, -0.2, 0.1]), 0.9, phys.gamma
+    Qh = np.zeros((E, 5, N ** 3))
+    Qh[:, 0], Qh[:, 1:4] = rho, (rho * u)[None, :, None]
+    Qh[:, 4] = p / (gam - 1) + 0.5 * rho * u @ u
+    Q = torch.tensor(Qh, device="cuda")
+    R = torch.empty_like(Q)
+    sh.mesh.residual(Params.from_phys(phys), FP64, Q, R, _ws(sh.mesh, FP64))
+    Rh = R.cpu().numpy().reshape(E, -1)
+    k = np.arange(E) % cfg.n_r
+    interior = (k >= 1) & (k < cfg.n_r - 1)
+    assert np.abs(Rh[interior]).max() < 1e-13 * 1.3 * N * N / sh.h_min

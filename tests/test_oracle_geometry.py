@@ -125,6 +125,7 @@ def test_cubed_sphere_connectivity(n, n_r):
     xyz, h20, nodes = _shell(n, n_r)
     E = 6 * n * n * n_r
     conn = Connectivity(xyz, h20, 4, 0.75, 1.0)
+    conn.ensure_perm(np.arange(E))
     assert np.sum(conn.wall == 1) == 6 * n * n and np.sum(conn.wall == 2) == 6 * n * n
     assert np.sum(conn.nbr >= 0) == 6 * E - 12 * n * n
     # pairing is symmetric and the point map is a bijection
