@@ -6,10 +6,13 @@ Tolerances (see the module docstring of gpu_common for the norm):
     error is its condition number times the backward error.  The test measures the condition
     number kappa_v of each variable on the oracle (relative change of R_v under a random relative
     input change of 1e-10, divided by 1e-10) and requires e_v <= 1e-12 * max(1, kappa_v).
-  * FP64 states after RK steps: the oracle trajectory is re-run with a relative 2^-53 random
-    perturbation of the state after every stage (a model of FP64 storage rounding); the spread of
-    the two oracle runs is the trajectory's own rounding noise, and the GPU must agree with the
-    oracle to max(1e-12, 10 x that spread).
+  * FP64 states after RK steps (compared on q' = Q - Q0): two error sources bound the agreement.
+    (a) the residual's backward error, amplified by the same condition numbers kappa_v, enters
+    each stage as dt R; summed over the run it is at most 1e-12 * kappa_v relative to q' as long as
+    the run changes q' by no more than its own size; (b) FP64 storage of the total state Q rounds
+    by eps |Q0| per stage, which is large relative to q' for density and energy; the test
+    measures (b) by re-running the oracle with a relative 2^-53 perturbation of the state after
+    every stage.  Tolerance: max(1e-12 * max(1, kappa_v), 10 x that spread).
   * FP32 perturbation path: 1e-5 relative L2 for the residual and for q' after steps.
 """
 import numpy as np
@@ -131,10 +134,13 @@ def test_rk_steps_match_oracle(prec):
     e, ev = rel_err(got, Qref - Q0, W)
     print(f"rk {n_steps} steps prec {prec}: rel err on q' {ev}")
     if prec == FP64:
+        from oracle.residual import residual
+
         noisy = _noisy_run(osh, Qinit, sh.dt, n_steps)
         _, spread = rel_err(noisy - Q0, Qref - Q0, W)
-        print(f"oracle rounding spread {spread}")
-        assert np.all(ev <= np.maximum(1e-12, 10.0 * spread))
+        kappa = _condition(osh, Qinit, residual(osh.disc, osh.ph, Qinit), W)
+        print(f"oracle rounding spread {spread}, residual condition {kappa}")
+        assert np.all(ev <= np.maximum(1e-12 * np.maximum(1.0, kappa), 10.0 * spread))
     else:
         assert e < 1e-5
 
