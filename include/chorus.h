@@ -132,6 +132,25 @@ chorus_status chorus_reduce(chorus_mesh mesh, const chorus_params* params, choru
 chorus_status chorus_timing_enable(chorus_mesh mesh, int enable);
 chorus_status chorus_timing_read(chorus_mesh mesh, void* stream, double* ms, int64_t* counts);
 
+/* chorus_residual without any device allocation by the caller or the library.  The paper has no
+ * counterpart: this is a library convenience.  Some callers cannot allocate device memory when they
+ * need a residual - for example an application that has handed all device memory to its own pool
+ * allocator, or a latency-critical loop that must not call cudaMalloc (which can synchronise the
+ * device).  They pass only the state Q and the output R (device, layout above); the face-trace
+ * scratch lives in one fixed 32 MiB device array inside the library, which every GPU that loads the
+ * library holds until the process exits.
+ *  - Size limit: E * 6 * 9 * N^2 words of the chosen precision must fit in 32 MiB (FP32 p = 3:
+ *    up to 9,709 elements; FP64 p = 3: up to 4,854).  Larger meshes return CHORUS_EINVAL before any
+ *    launch; use chorus_residual with a workspace for them.
+ *  - Set-up: the first call on a device looks up the array's device address with that device
+ *    current; make that first call before any stream capture.  Call with the mesh's device current.
+ *  - Sharing: all calls share the one array and it keeps the previous call's contents (every call
+ *    overwrites all it reads, nothing needs to start at zero).  Calls that overlap on the GPU (other
+ *    streams, other threads) race on it and must be serialised by the caller.
+ *  - FP32_PERT needs chorus_prepare with the same params first, as chorus_residual does. */
+chorus_status chorus_residual_noalloc(chorus_mesh mesh, const chorus_params* params, chorus_precision prec,
+                                      const void* Q, void* R, void* stream);
+
 /* Synchronise the stream and report a pending device-side error flag (CHORUS_ETIMEOUT). */
 chorus_status chorus_check(chorus_mesh mesh, void* stream);
 

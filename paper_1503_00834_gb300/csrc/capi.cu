@@ -674,3 +674,74 @@ chorus_status chorus_check(chorus_mesh m, void* stream) {
 }
 
 }  // extern "C"
+
+// ---------------------------------------------------------------- residual without allocation
+//
+// chorus_residual needs a caller-allocated workspace for the face traces.  Some callers cannot
+// allocate device memory at the point where they want a residual, so this variant keeps its
+// scratch in one file-scope device array of fixed size instead.  The array exists once per GPU
+// that loads this library and stays allocated until the process exits.  Its device address is
+// looked up once per device (cudaGetSymbolAddress, with that device current) on the first call;
+// the host-side symbol is only a stand-in and is never handed to a kernel.
+#include <mutex>
+
+namespace {
+
+constexpr size_t kNoAllocScratchBytes = size_t(32) << 20;  // 32 MiB
+__device__ __align__(256) unsigned char g_noalloc_scratch[kNoAllocScratchBytes];
+
+constexpr int kNoAllocMaxDevices = 64;
+void* g_noalloc_ptr[kNoAllocMaxDevices] = {};
+std::mutex g_noalloc_mu;
+
+// Device address of the scratch array on the current device (set up on first use per device).
+chorus_status noalloc_scratch(void** out) {
+  int dev = -1;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kNoAllocMaxDevices) return CHORUS_ECUDA;
+  std::lock_guard<std::mutex> lock(g_noalloc_mu);
+  if (!g_noalloc_ptr[dev]) {
+    void* p = nullptr;
+    if (cudaGetSymbolAddress(&p, g_noalloc_scratch) != cudaSuccess || p == nullptr) return CHORUS_ECUDA;
+    g_noalloc_ptr[dev] = p;
+  }
+  *out = g_noalloc_ptr[dev];
+  return CHORUS_OK;
+}
+
+}  // namespace
+
+extern "C" chorus_status chorus_residual_noalloc(chorus_mesh m, const chorus_params* P, chorus_precision prec,
+                                                 const void* Q, void* R, void* stream) {
+  if (!m || !Q || !R || !params_ok(P)) return CHORUS_EINVAL;
+  if (prec != CHORUS_FP64 && prec != CHORUS_FP32_PERT) return CHORUS_EINVAL;
+  const size_t N2 = (size_t)m->N * m->N, E = (size_t)m->E;
+  const size_t word = prec == CHORUS_FP64 ? sizeof(double) : sizeof(float);
+  const size_t nT = E * 6 * 5 * N2, nTv = E * 6 * 4 * N2;
+  if ((nT + nTv) * word > kNoAllocScratchBytes) return CHORUS_EINVAL;  // mesh too large for the scratch
+  if (prec == CHORUS_FP32_PERT && (!m->prepared || !same_params(m->prep, *P))) return CHORUS_EINVAL;
+  void* scratch = nullptr;
+  chorus_status s = noalloc_scratch(&scratch);
+  if (s != CHORUS_OK) return s;
+  cudaStream_t st = (cudaStream_t)stream;
+  if (prec == CHORUS_FP64) {
+    const PhysArg<double> ph = phys_arg<double>(*P, m->r_inner, m->r_outer);
+    const MeshArg<double> ma = mesh_arg<double>(m);
+    double* T = (double*)scratch;
+    double* Tv = T + nT;
+    CHK(m->L.trace64(ma, m->ops64, (const double*)Q, T, st));
+    CHK(m->L.grad64(ma, m->ops64, ph, (const double*)Q, T, Tv, nullptr, m->d_err, st));
+    CHK(m->L.resid64(ma, m->ops64, ph, (const double*)Q, T, Tv, (double*)R, nullptr, nullptr, 0.0, 1.0, 0.0,
+                     kModeResidual, m->d_err, st));
+    return CHORUS_OK;
+  }
+  const PhysArg<float> ph = phys_arg<float>(*P, m->r_inner, m->r_outer);
+  const MeshArg<float> ma = mesh_arg<float>(m);
+  const BgArg bg = bg_arg(m);
+  float* T = (float*)scratch;
+  float* Tv = T + nT;
+  CHK(m->L.trace32(ma, m->ops32, (const float*)Q, T, st));
+  CHK(m->L.grad32(ma, m->ops32, ph, bg, (const float*)Q, T, Tv, m->d_err, st));
+  CHK(m->L.resid32(ma, m->ops32, ph, bg, (const float*)Q, T, Tv, (float*)R, nullptr, nullptr, 0.0f, 1.0f, 0.0f,
+                   kModeResidual, m->d_err, st));
+  return CHORUS_OK;
+}

@@ -25,7 +25,7 @@ STATUS = {0: "ok", 1: "invalid argument", 2: "out of memory", 3: "CUDA error", 4
 # every symbol declared in include/chorus.h
 EXPORTS = ("chorus_mesh_create", "chorus_mesh_destroy", "chorus_mesh_info", "chorus_prepare", "chorus_state_init",
            "chorus_residual", "chorus_rk_workspace_bytes", "chorus_rk_step", "chorus_reduce", "chorus_check",
-           "chorus_strerror", "chorus_timing_enable", "chorus_timing_read")
+           "chorus_strerror", "chorus_timing_enable", "chorus_timing_read", "chorus_residual_noalloc")
 
 
 class ChorusError(RuntimeError):
@@ -72,6 +72,7 @@ def load() -> ctypes.CDLL:
         "chorus_strerror": (ctypes.c_char_p, [i32]),
         "chorus_timing_enable": (i32, [vp, i32]),
         "chorus_timing_read": (i32, [vp, vp, P(f64), P(i64)]),
+        "chorus_residual_noalloc": (i32, [vp, P(Params), i32, vp, vp, vp]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(lib, name)
