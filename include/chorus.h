@@ -117,11 +117,29 @@ size_t chorus_rk_workspace_bytes(chorus_mesh mesh, chorus_precision prec);
 chorus_status chorus_rk_step(chorus_mesh mesh, const chorus_params* params, chorus_precision prec,
                              void* Q, void* workspace, double dt, int64_t n_steps, void* stream);
 
+/* n_steps steps of an explicit SSP scheme, in place on Q.  scheme 0: the SSP-RK3 of
+ * chorus_rk_step; scheme 1: the five-stage fourth-order SSP-RK(5,4) of Spiteri and Ruuth that the
+ * paper integrates with (Section 7.4; Shu-Osher form u1 = u + b10 dt L(u), ...,
+ * u^{n+1} = a52 u2 + a53 u3 + b53 dt L(u3) + a54 u4 + b54 dt L(u4), published coefficients).
+ * Workspace as for chorus_rk_step. */
+chorus_status chorus_rk_step_scheme(chorus_mesh mesh, const chorus_params* params, chorus_precision prec,
+                                    int scheme, void* Q, void* workspace, double dt, int64_t n_steps,
+                                    void* stream);
+
 /* FP64 volume integrals of Q (total state): out[0] mass, out[1] total energy, out[2] kinetic
  * energy sum |m|^2/(2 rho), out[3] |L| with L = integral of x cross (rho u) (Section 6, Eq. 32).
  * out: host double[4].  Synchronises the stream; returns CHORUS_ENAN on non-finite results. */
 chorus_status chorus_reduce(chorus_mesh mesh, const chorus_params* params, chorus_precision prec,
                             const void* Q, double* out, void* stream);
+
+/* Angular-momentum correction (Section 6): L = integral of x cross (rho u) (Eq. 32), moments of
+ * inertia I_x = integral of rho (y^2 + z^2) etc., delta Omega_i = L_i / I_i (Eq. 33), and the
+ * velocity update of Eq. 34 (u -= delta Omega x r) at every solution point, in place on Q; density
+ * and pressure are kept (the total energy takes the new kinetic energy).  Integrals in FP64 with
+ * the solution-point quadrature.  domega: host double[3] receiving delta Omega (the call then
+ * synchronises the stream) or NULL (fully asynchronous).  FP32_PERT needs chorus_prepare. */
+chorus_status chorus_am_correct(chorus_mesh mesh, const chorus_params* params, chorus_precision prec,
+                                void* Q, double* domega, void* stream);
 
 /* Kernel timing for measurement.  While enabled, every kernel that chorus_residual and
  * chorus_rk_step launch is bracketed by a pair of CUDA events recorded on the call's stream (the

@@ -32,6 +32,7 @@ def _nvcc() -> str:
 
 def _headers_mtime() -> float:
     paths = [os.path.join(CSRC, f) for f in os.listdir(CSRC) if f.endswith((".h", ".cuh"))]
+    paths.append(os.path.abspath(__file__))
     paths.append(os.path.join(INCLUDE, "chorus.h"))
     return max(os.path.getmtime(p) for p in paths)
 

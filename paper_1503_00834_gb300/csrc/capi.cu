@@ -232,6 +232,72 @@ __global__ void k_reduce_final(int nb, const double* __restrict__ part, double* 
   }
 }
 
+// angular momentum L = sum w x cross m and moments of inertia I_i = sum w rho (|x|^2 - x_i^2)
+// (Section 6, Eq. 32), per-block partial sums in FP64
+template <class R>
+__global__ void k_am_partial(int64_t n_pts, int N3, const R* __restrict__ q, const double* __restrict__ Q0,
+                             const double* __restrict__ wJ, const double* __restrict__ x, double* __restrict__ part) {
+  __shared__ double sh[6][256];
+  double acc[6] = {0, 0, 0, 0, 0, 0};
+  for (int64_t g = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; g < n_pts; g += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t e = g / N3, pt = g % N3;
+    double rho = (double)q[(e * 5) * N3 + pt];
+    if (Q0) rho += Q0[(e * 5) * N3 + pt];
+    const double m0 = (double)q[(e * 5 + 1) * N3 + pt], m1 = (double)q[(e * 5 + 2) * N3 + pt],
+                 m2 = (double)q[(e * 5 + 3) * N3 + pt];  // background momentum is zero
+    const double w = wJ[g];
+    const double x0 = x[(e * 3) * N3 + pt], x1 = x[(e * 3 + 1) * N3 + pt], x2 = x[(e * 3 + 2) * N3 + pt];
+    acc[0] += w * (x1 * m2 - x2 * m1);
+    acc[1] += w * (x2 * m0 - x0 * m2);
+    acc[2] += w * (x0 * m1 - x1 * m0);
+    acc[3] += w * rho * (x1 * x1 + x2 * x2);
+    acc[4] += w * rho * (x0 * x0 + x2 * x2);
+    acc[5] += w * rho * (x0 * x0 + x1 * x1);
+  }
+  for (int c = 0; c < 6; ++c) sh[c][threadIdx.x] = acc[c];
+  __syncthreads();
+  for (int s = blockDim.x / 2; s > 0; s >>= 1) {
+    if (threadIdx.x < s)
+      for (int c = 0; c < 6; ++c) sh[c][threadIdx.x] += sh[c][threadIdx.x + s];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0)
+    for (int c = 0; c < 6; ++c) part[blockIdx.x * 6 + c] = sh[c][0];
+}
+
+// out[0..5] = (L, I) summed in a fixed order, out[6..8] = delta Omega = L / I (Eq. 33)
+__global__ void k_am_final(int nb, const double* __restrict__ part, double* __restrict__ out) {
+  if (threadIdx.x == 0) {
+    double s[6] = {0, 0, 0, 0, 0, 0};
+    for (int b = 0; b < nb; ++b)
+      for (int c = 0; c < 6; ++c) s[c] += part[b * 6 + c];
+    for (int c = 0; c < 6; ++c) out[c] = s[c];
+    for (int c = 0; c < 3; ++c) out[6 + c] = s[3 + c] > 0.0 ? s[c] / s[3 + c] : 0.0;
+  }
+}
+
+// velocity update of Eq. 34 (u -= delta Omega x r), density and pressure kept
+template <class R>
+__global__ void k_am_update(int64_t n_pts, int N3, R* __restrict__ q, const double* __restrict__ Q0,
+                            const double* __restrict__ x, const double* __restrict__ dO) {
+  const int64_t g = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (g >= n_pts) return;
+  const int64_t e = g / N3, pt = g % N3;
+  double rho = (double)q[(e * 5) * N3 + pt];
+  if (Q0) rho += Q0[(e * 5) * N3 + pt];
+  const double x0 = x[(e * 3) * N3 + pt], x1 = x[(e * 3 + 1) * N3 + pt], x2 = x[(e * 3 + 2) * N3 + pt];
+  const double w0 = dO[0], w1 = dO[1], w2 = dO[2];
+  const double c0 = w1 * x2 - w2 * x1, c1 = w2 * x0 - w0 * x2, c2 = w0 * x1 - w1 * x0;  // delta Omega x r
+  double m[3], mn[3];
+  for (int a = 0; a < 3; ++a) m[a] = (double)q[(e * 5 + 1 + a) * N3 + pt];
+  mn[0] = m[0] - rho * c0;
+  mn[1] = m[1] - rho * c1;
+  mn[2] = m[2] - rho * c2;
+  const double dke = 0.5 * ((mn[0] * mn[0] + mn[1] * mn[1] + mn[2] * mn[2]) - (m[0] * m[0] + m[1] * m[1] + m[2] * m[2])) / rho;
+  for (int a = 0; a < 3; ++a) q[(e * 5 + 1 + a) * N3 + pt] = (R)mn[a];
+  q[(e * 5 + 4) * N3 + pt] = (R)((double)q[(e * 5 + 4) * N3 + pt] + dke);
+}
+
 constexpr int kRedBlocks = 1024;
 
 template <class R>
@@ -315,8 +381,8 @@ void free_mesh(chorus_mesh_s* m) {
 size_t ws_words(const chorus_mesh_s* m) {
   const size_t N = m->N, E = m->E;
   const size_t N2 = N * N, N3 = N2 * N;
-  // stage buffer + two trace buffers + viscous normal-flux traces
-  return E * 5 * N3 + 2 * E * 6 * 5 * N2 + E * 6 * 4 * N2;
+  // stage buffer + two trace buffers + viscous normal-flux traces + two more stage buffers (RK(5,4))
+  return 3 * E * 5 * N3 + 2 * E * 6 * 5 * N2 + E * 6 * 4 * N2;
 }
 
 template <class R>
@@ -325,6 +391,8 @@ struct Ws {
   R* Ta;
   R* Tb;
   R* Tv;
+  R* A;
+  R* B;
 };
 
 template <class R>
@@ -337,6 +405,8 @@ Ws<R> split_ws(const chorus_mesh_s* m, void* w) {
   r.Ta = r.s + E * 5 * N3;
   r.Tb = r.Ta + E * 6 * 5 * N2;
   r.Tv = r.Tb + E * 6 * 5 * N2;
+  r.A = r.Tv + E * 6 * 4 * N2;
+  r.B = r.A + E * 5 * N3;
   return r;
 }
 
@@ -416,7 +486,7 @@ chorus_status chorus_mesh_create(int64_t n_nodes, const double* node_xyz, int64_
             dev_alloc(&m->d_x64, 3 * nP) == cudaSuccess && dev_alloc(&m->d_wJ, nP) == cudaSuccess &&
             dev_alloc(&m->d_Sf32, nS) == cudaSuccess && dev_alloc(&m->d_invJ32, nP) == cudaSuccess &&
             dev_alloc(&m->d_x32, 3 * nP) == cudaSuccess && dev_alloc(&m->d_err, 4) == cudaSuccess &&
-            dev_alloc(&m->d_red, (size_t)kRedBlocks * 6 + 8) == cudaSuccess;
+            dev_alloc(&m->d_red, (size_t)kRedBlocks * 6 + 16) == cudaSuccess;
   if (!ok) {
     free_mesh(m);
     return CHORUS_ENOMEM;
@@ -498,7 +568,7 @@ chorus_status chorus_prepare(chorus_mesh m, const chorus_params* P, void* stream
   if (ce == cudaSuccess) ce = m->L.trace64(ma, m->ops64, m->d_Q0, T, st);
   if (ce == cudaSuccess) ce = m->L.grad64(ma, m->ops64, ph, m->d_Q0, T, Tv, gr, m->d_err, st);
   if (ce == cudaSuccess)
-    ce = m->L.resid64(ma, m->ops64, ph, m->d_Q0, T, Tv, R0, nullptr, nullptr, 0.0, 1.0, 0.0, kModeResidual, m->d_err, st);
+    ce = m->L.resid64(ma, m->ops64, ph, m->d_Q0, T, Tv, R0, nullptr, RkCoef<double>{}, 0.0, kModeResidual, m->d_err, st);
   if (ce == cudaSuccess) {
     k_d2f<<<grid1(5 * nP), 256, 0, st>>>((int64_t)(5 * nP), R0, m->d_R0);
     k_d2f<<<grid1(3 * nP), 256, 0, st>>>((int64_t)(3 * nP), gr, m->d_grho0);
@@ -540,7 +610,7 @@ chorus_status chorus_residual(chorus_mesh m, const chorus_params* P, chorus_prec
     CHK(timed(m, 0, st, [&] { return m->L.trace64(ma, m->ops64, (const double*)Q, w.Ta, st); }));
     CHK(timed(m, 1, st, [&] { return m->L.grad64(ma, m->ops64, ph, (const double*)Q, w.Ta, w.Tv, nullptr, m->d_err, st); }));
     CHK(timed(m, 2, st, [&] {
-      return m->L.resid64(ma, m->ops64, ph, (const double*)Q, w.Ta, w.Tv, (double*)R, nullptr, nullptr, 0.0, 1.0, 0.0,
+      return m->L.resid64(ma, m->ops64, ph, (const double*)Q, w.Ta, w.Tv, (double*)R, nullptr, RkCoef<double>{}, 0.0,
                           kModeResidual, m->d_err, st);
     }));
     return CHORUS_OK;
@@ -554,37 +624,84 @@ chorus_status chorus_residual(chorus_mesh m, const chorus_params* P, chorus_prec
   CHK(timed(m, 0, st, [&] { return m->L.trace32(ma, m->ops32, (const float*)Q, w.Ta, st); }));
   CHK(timed(m, 1, st, [&] { return m->L.grad32(ma, m->ops32, ph, bg, (const float*)Q, w.Ta, w.Tv, m->d_err, st); }));
   CHK(timed(m, 2, st, [&] {
-    return m->L.resid32(ma, m->ops32, ph, bg, (const float*)Q, w.Ta, w.Tv, (float*)R, nullptr, nullptr, 0.0f, 1.0f,
-                        0.0f, kModeResidual, m->d_err, st);
+    return m->L.resid32(ma, m->ops32, ph, bg, (const float*)Q, w.Ta, w.Tv, (float*)R, nullptr, RkCoef<float>{}, 0.0f,
+                        kModeResidual, m->d_err, st);
   }));
   return CHORUS_OK;
 }
 
-chorus_status chorus_rk_step(chorus_mesh m, const chorus_params* P, chorus_precision prec, void* Q, void* workspace,
-                             double dt, int64_t n_steps, void* stream) {
-  if (!m || !Q || !workspace || !params_ok(P) || !(dt > 0.0) || !std::isfinite(dt) || n_steps < 0) return CHORUS_EINVAL;
+}  // extern "C"
+
+namespace {
+
+// One stage of an explicit SSP scheme: residual of `src`, fused combination into `dst` (and
+// optionally a second output), traces of `dst` for the next stage.
+struct Stage {
+  int src, dst;           // buffer ids: 0 u (the caller's state), 1 s, 2 A, 3 B
+  int un;                 // first extra input
+  double a, b, c;         // dst = a un + b src + c dt L(src)
+  int un2, out2;          // -1: none
+  double a2, b2, c2;      // out2 = a2 un2 + b2 src + c2 dt L(src)
+};
+
+// SSP-RK3 (Shu-Osher) and SSP-RK(5,4) (Spiteri-Ruuth) stage lists
+const std::vector<Stage>& stages_of(int scheme) {
+  static const std::vector<Stage> rk3 = {
+      {0, 1, 0, 0.0, 1.0, 1.0, -1, -1, 0, 0, 0},
+      {1, 1, 0, 0.75, 0.25, 0.25, -1, -1, 0, 0, 0},
+      {1, 0, 0, 1.0 / 3.0, 2.0 / 3.0, 2.0 / 3.0, -1, -1, 0, 0, 0},
+  };
+  static const std::vector<Stage> rk54 = {
+      {0, 1, 0, 0.0, 1.0, 0.391752226571890, -1, -1, 0, 0, 0},
+      {1, 2, 0, 0.444370493651235, 0.555629506348765, 0.368410593050371, -1, -1, 0, 0, 0},
+      {2, 1, 0, 0.620101851488403, 0.379898148511597, 0.251891774271694, -1, -1, 0, 0, 0},
+      {1, 1, 0, 0.178079954393132, 0.821920045606868, 0.544974750228521, 2, 3, 0.517231671970585,
+       0.096059710526147, 0.063692468666290},
+      {1, 0, 3, 1.0, 0.386708617503269, 0.226007483236906, -1, -1, 0, 0, 0},
+  };
+  return scheme == 1 ? rk54 : rk3;
+}
+
+template <class R, class Grad, class Resid, class Trace>
+chorus_status run_rk(chorus_mesh_s* m, R* u, const Ws<R>& w, double dt, int64_t n_steps, int scheme, cudaStream_t st,
+                     Grad grad, Resid resid, Trace trace) {
+  R* buf[4] = {u, w.s, w.A, w.B};
+  R *Tc = w.Ta, *Tn = w.Tb;
+  CHK(timed(m, 0, st, [&] { return trace(u, Tc); }));
+  const auto& stg = stages_of(scheme);
+  for (int64_t n = 0; n < n_steps; ++n)
+    for (const Stage& g : stg) {
+      RkCoef<R> c{buf[g.un], (R)g.a, (R)g.b, (R)g.c, g.un2 >= 0 ? buf[g.un2] : nullptr,
+                  g.out2 >= 0 ? buf[g.out2] : nullptr, (R)g.a2, (R)g.b2, (R)g.c2};
+      CHK(timed(m, 1, st, [&] { return grad(buf[g.src], Tc); }));
+      CHK(timed(m, 2, st, [&] { return resid(buf[g.src], Tc, buf[g.dst], Tn, c); }));
+      std::swap(Tc, Tn);
+    }
+  return CHORUS_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+chorus_status chorus_rk_step_scheme(chorus_mesh m, const chorus_params* P, chorus_precision prec, int scheme, void* Q,
+                                    void* workspace, double dt, int64_t n_steps, void* stream) {
+  if (!m || !Q || !workspace || !params_ok(P) || !(dt > 0.0) || !std::isfinite(dt) || n_steps < 0 ||
+      (scheme != 0 && scheme != 1))
+    return CHORUS_EINVAL;
   if (n_steps == 0) return CHORUS_OK;
   cudaStream_t st = (cudaStream_t)stream;
-  static const double ca[3] = {0.0, 0.75, 1.0 / 3.0};
-  static const double cb[3] = {1.0, 0.25, 2.0 / 3.0};
   if (prec == CHORUS_FP64) {
     const PhysArg<double> ph = phys_arg<double>(*P, m->r_inner, m->r_outer);
     const MeshArg<double> ma = mesh_arg<double>(m);
     Ws<double> w = split_ws<double>(m, workspace);
-    double* u = (double*)Q;
-    double *Tc = w.Ta, *Tn = w.Tb;
-    CHK(timed(m, 0, st, [&] { return m->L.trace64(ma, m->ops64, u, Tc, st); }));
-    for (int64_t n = 0; n < n_steps; ++n)
-      for (int k = 0; k < 3; ++k) {
-        const double* src = k == 0 ? u : w.s;
-        double* dst = k == 2 ? u : w.s;
-        CHK(timed(m, 1, st, [&] { return m->L.grad64(ma, m->ops64, ph, src, Tc, w.Tv, nullptr, m->d_err, st); }));
-        CHK(timed(m, 2, st, [&] {
-          return m->L.resid64(ma, m->ops64, ph, src, Tc, w.Tv, dst, Tn, u, ca[k], cb[k], dt, kModeRK, m->d_err, st);
-        }));
-        std::swap(Tc, Tn);
-      }
-    return CHORUS_OK;
+    return run_rk<double>(
+        m, (double*)Q, w, dt, n_steps, scheme, st,
+        [&](const double* q, const double* T) { return m->L.grad64(ma, m->ops64, ph, q, T, w.Tv, nullptr, m->d_err, st); },
+        [&](const double* q, const double* T, double* dst, double* Tn, const RkCoef<double>& c) {
+          return m->L.resid64(ma, m->ops64, ph, q, T, w.Tv, dst, Tn, c, dt, kModeRK, m->d_err, st);
+        },
+        [&](const double* q, double* T) { return m->L.trace64(ma, m->ops64, q, T, st); });
   }
   if (prec != CHORUS_FP32_PERT) return CHORUS_EINVAL;
   if (!m->prepared || !same_params(m->prep, *P)) return CHORUS_EINVAL;
@@ -592,21 +709,18 @@ chorus_status chorus_rk_step(chorus_mesh m, const chorus_params* P, chorus_preci
   const MeshArg<float> ma = mesh_arg<float>(m);
   const BgArg bg = bg_arg(m);
   Ws<float> w = split_ws<float>(m, workspace);
-  float* u = (float*)Q;
-  float *Tc = w.Ta, *Tn = w.Tb;
-  CHK(timed(m, 0, st, [&] { return m->L.trace32(ma, m->ops32, u, Tc, st); }));
-  for (int64_t n = 0; n < n_steps; ++n)
-    for (int k = 0; k < 3; ++k) {
-      const float* src = k == 0 ? u : w.s;
-      float* dst = k == 2 ? u : w.s;
-      CHK(timed(m, 1, st, [&] { return m->L.grad32(ma, m->ops32, ph, bg, src, Tc, w.Tv, m->d_err, st); }));
-      CHK(timed(m, 2, st, [&] {
-        return m->L.resid32(ma, m->ops32, ph, bg, src, Tc, w.Tv, dst, Tn, u, (float)ca[k], (float)cb[k], (float)dt,
-                            kModeRK, m->d_err, st);
-      }));
-      std::swap(Tc, Tn);
-    }
-  return CHORUS_OK;
+  return run_rk<float>(
+      m, (float*)Q, w, dt, n_steps, scheme, st,
+      [&](const float* q, const float* T) { return m->L.grad32(ma, m->ops32, ph, bg, q, T, w.Tv, m->d_err, st); },
+      [&](const float* q, const float* T, float* dst, float* Tn, const RkCoef<float>& c) {
+        return m->L.resid32(ma, m->ops32, ph, bg, q, T, w.Tv, dst, Tn, c, (float)dt, kModeRK, m->d_err, st);
+      },
+      [&](const float* q, float* T) { return m->L.trace32(ma, m->ops32, q, T, st); });
+}
+
+chorus_status chorus_rk_step(chorus_mesh m, const chorus_params* P, chorus_precision prec, void* Q, void* workspace,
+                             double dt, int64_t n_steps, void* stream) {
+  return chorus_rk_step_scheme(m, P, prec, 0, Q, workspace, dt, n_steps, stream);
 }
 
 chorus_status chorus_reduce(chorus_mesh m, const chorus_params* P, chorus_precision prec, const void* Q, double* out,
@@ -637,6 +751,33 @@ chorus_status chorus_reduce(chorus_mesh m, const chorus_params* P, chorus_precis
   unsigned err = 0;
   CHK(cudaMemcpy(&err, m->d_err, sizeof(unsigned), cudaMemcpyDeviceToHost));
   return err ? CHORUS_ETIMEOUT : CHORUS_OK;
+}
+
+chorus_status chorus_am_correct(chorus_mesh m, const chorus_params* P, chorus_precision prec, void* Q,
+                                double* domega, void* stream) {
+  if (!m || !Q) return CHORUS_EINVAL;
+  cudaStream_t st = (cudaStream_t)stream;
+  const int N3 = m->N * m->N * m->N;
+  const int64_t nP = m->E * N3;
+  double* out = m->d_red + kRedBlocks * 6;
+  if (prec == CHORUS_FP64) {
+    k_am_partial<double><<<kRedBlocks, 256, 0, st>>>(nP, N3, (const double*)Q, nullptr, m->d_wJ, m->d_x64, m->d_red);
+    k_am_final<<<1, 32, 0, st>>>(kRedBlocks, m->d_red, out);
+    k_am_update<double><<<grid1(nP), 256, 0, st>>>(nP, N3, (double*)Q, nullptr, m->d_x64, out + 6);
+  } else if (prec == CHORUS_FP32_PERT) {
+    if (!P || !m->prepared || !same_params(m->prep, *P)) return CHORUS_EINVAL;
+    k_am_partial<float><<<kRedBlocks, 256, 0, st>>>(nP, N3, (const float*)Q, m->d_Q0, m->d_wJ, m->d_x64, m->d_red);
+    k_am_final<<<1, 32, 0, st>>>(kRedBlocks, m->d_red, out);
+    k_am_update<float><<<grid1(nP), 256, 0, st>>>(nP, N3, (float*)Q, m->d_Q0, m->d_x64, out + 6);
+  } else {
+    return CHORUS_EINVAL;
+  }
+  CHK(cudaGetLastError());
+  if (domega) {
+    CHK(cudaMemcpyAsync(domega, out + 6, 3 * sizeof(double), cudaMemcpyDeviceToHost, st));
+    CHK(cudaStreamSynchronize(st));
+  }
+  return CHORUS_OK;
 }
 
 chorus_status chorus_timing_enable(chorus_mesh m, int enable) {
@@ -730,7 +871,7 @@ extern "C" chorus_status chorus_residual_noalloc(chorus_mesh m, const chorus_par
     double* Tv = T + nT;
     CHK(m->L.trace64(ma, m->ops64, (const double*)Q, T, st));
     CHK(m->L.grad64(ma, m->ops64, ph, (const double*)Q, T, Tv, nullptr, m->d_err, st));
-    CHK(m->L.resid64(ma, m->ops64, ph, (const double*)Q, T, Tv, (double*)R, nullptr, nullptr, 0.0, 1.0, 0.0,
+    CHK(m->L.resid64(ma, m->ops64, ph, (const double*)Q, T, Tv, (double*)R, nullptr, RkCoef<double>{}, 0.0,
                      kModeResidual, m->d_err, st));
     return CHORUS_OK;
   }
@@ -741,7 +882,7 @@ extern "C" chorus_status chorus_residual_noalloc(chorus_mesh m, const chorus_par
   float* Tv = T + nT;
   CHK(m->L.trace32(ma, m->ops32, (const float*)Q, T, st));
   CHK(m->L.grad32(ma, m->ops32, ph, bg, (const float*)Q, T, Tv, m->d_err, st));
-  CHK(m->L.resid32(ma, m->ops32, ph, bg, (const float*)Q, T, Tv, (float*)R, nullptr, nullptr, 0.0f, 1.0f, 0.0f,
+  CHK(m->L.resid32(ma, m->ops32, ph, bg, (const float*)Q, T, Tv, (float*)R, nullptr, RkCoef<float>{}, 0.0f,
                    kModeResidual, m->d_err, st));
   return CHORUS_OK;
 }

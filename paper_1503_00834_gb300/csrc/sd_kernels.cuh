@@ -1,253 +1,118 @@
 // Spectral-difference residual kernels for one order N = p + 1 (paper Sections 3 and 5).
 //
 // One CTA processes EPB elements; each element is handled by N*N threads, thread `ln` owning the
-// line (t1, t2) = (ln % N, ln / N) of every direction (xi-line (j,k), eta-line (i,k), zeta-line
-// (i,j)).  A thread therefore does the whole 1D work of its line - interpolation to the N+1 flux
-// points (Eq. 17), fluxes, face common fluxes at the two end points, derivative back to the N
-// solution points (Eq. 18) - in registers; shared memory carries the element data between the
-// three directional sweeps.  The element's state block is staged into shared memory with a 1D
-// bulk TMA copy (cp.async.bulk + mbarrier) when it is 16-byte aligned.
+// line (a, b) = (ln % N, ln / N) of every direction (xi-line (j,k), eta-line (i,k), zeta-line
+// (i,j)).  A thread does the whole 1D work of its line in registers: interpolation to the N+1
+// flux points (Eq. 17), fluxes, the common fluxes at the two end points, and the derivative back
+// to the N solution points (Eq. 18).  Shared memory links the three directional sweeps.
 //
-// Two physics forms share the kernels:
-//   PERT = false, R = double : Q is the total conserved state; plain fluxes.
-//   PERT = true,  R = float  : Q is q' = Q - Q0 about the polytrope at rest; every nonlinear
-//                              term is written as an exact algebraic difference F(Q0+q') - F(Q0)
-//                              so that FP32 rounding is relative to the perturbation, and the
-//                              FP64 background residual R(Q0) is added at the end.
+// Shared memory per element: the staged state (bulk TMA copy per element block, linear layout),
+// the background tables (perturbation form), the lifted gradients and the divergence accumulator.
+// Element blocks are padded so that the two elements of a warp at p = 3 use opposite halves of the
+// banks, and for N = 4 in FP32 the computed arrays are XOR-swizzled so that xi-, eta- and
+// zeta-line accesses are conflict free.  Neighbour face data are gathered from global memory
+// straight into registers when a sweep needs them.
 #pragma once
-#include <cuda_runtime.h>
-#include <stdint.h>
-
-#include "internal.h"
+#include "sd_device.cuh"
 
 namespace chorus {
 
-// ------------------------------------------------------------------ async-copy helpers
+// ------------------------------------------------------------------ layout helpers
 
-__device__ __forceinline__ uint32_t smem_addr(const void* p) {
-  return static_cast<uint32_t>(__cvta_generic_to_shared(p));
-}
-
-__device__ __forceinline__ void mbar_init(uint64_t* bar) {
-  asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_addr(bar)) : "memory");
-  asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
-  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-}
-
-__device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, uint32_t bytes) {
-  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_addr(bar)), "r"(bytes)
-               : "memory");
-}
-
-// 1D bulk copy global -> shared, completion signalled on the mbarrier (byte count).
-__device__ __forceinline__ void bulk_g2s(void* dst, const void* src, uint32_t bytes, uint64_t* bar) {
-  asm volatile(
-      "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
-          smem_addr(dst)),
-      "l"(src), "r"(bytes), "r"(smem_addr(bar))
-      : "memory");
-}
-
-// Bounded wait on phase 0 of the barrier.  Returns false (and sets *err) if the limit ran out.
-__device__ __forceinline__ bool mbar_wait0(uint64_t* bar, unsigned* err) {
-  const uint32_t a = smem_addr(bar);
-  for (uint32_t it = 0; it < (1u << 24); ++it) {
-    uint32_t ok;
-    asm volatile(
-        "{ .reg .pred p; mbarrier.try_wait.parity.shared::cta.b64 p, [%1], 0; selp.b32 %0, 1, 0, p; }"
-        : "=r"(ok)
-        : "r"(a)
-        : "memory");
-    if (ok) return true;
-    if (it > 64) __nanosleep(64);
-  }
-  if (err) atomicOr(err, 1u);
-  return false;
-}
-
-// ------------------------------------------------------------------ index helpers
-
-// point index of position s along line `ln` of direction d
-template <int N>
-__device__ __forceinline__ int pt_of(int d, int ln, int s) {
-  const int t1 = ln % N, t2 = ln / N;
-  if (d == 0) return s + N * t1 + N * N * t2;
-  if (d == 1) return t1 + N * s + N * N * t2;
-  return t1 + N * t2 + N * N * s;
-}
-
-// neighbour face-point index of own face point t under the orientation bits (swap, flip1, flip2)
-template <int N>
-__device__ __forceinline__ int map_face_pt(int t, int orient) {
-  const int t1 = t % N, t2 = t / N;
-  int a = (orient & 4) ? t2 : t1;
-  int b = (orient & 4) ? t1 : t2;
-  if (orient & 2) a = N - 1 - a;
-  if (orient & 1) b = N - 1 - b;
-  return a + N * b;
-}
-
-// ------------------------------------------------------------------ point physics
-
+// Count of R words padded to a multiple of 16 bytes whose byte size is 64 mod 128.
 template <class R>
-struct Pt {
-  R rho;    // total density
-  R rhop;   // the form's density variable (rho or rho')
-  R u[3];   // velocity
-  R p;      // the form's pressure variable (p or p')
-  R ptot;   // total pressure
-  R Etot;   // total energy
-};
+constexpr int pad_stride(int count) {
+  int bytes = (count * (int)sizeof(R) + 15) / 16 * 16;
+  const int r = bytes % 128;
+  bytes += (64 - r + 128) % 128;
+  return bytes / (int)sizeof(R);
+}
 
-template <bool PERT, class R>
-__device__ __forceinline__ Pt<R> point_state(const R q[5], R rho0, R E0, const PhysArg<R>& ph) {
-  Pt<R> s;
-  s.rhop = q[0];
-  s.rho = PERT ? rho0 + q[0] : q[0];
-  const R ir = R(1) / s.rho;
-  s.u[0] = q[1] * ir;
-  s.u[1] = q[2] * ir;
-  s.u[2] = q[3] * ir;
-  const R ke = R(0.5) * (q[1] * s.u[0] + q[2] * s.u[1] + q[3] * s.u[2]);
-  s.p = ph.gm1 * (q[4] - ke);
-  if (PERT) {
-    s.ptot = ph.gm1 * E0 + s.p;
-    s.Etot = E0 + q[4];
+// Shared-memory index of solution point (i,j,k) within one component array of the computed arrays.
+template <int N, class R>
+__device__ __forceinline__ int sidx(int i, int j, int k) {
+  if (N == 4 && sizeof(R) == 4) return i + 4 * ((j ^ k) & 3) + 16 * k;
+  return i + N * j + N * N * k;
+}
+
+// (i,j,k) of position s on line ln of direction D
+template <int N, int D>
+__device__ __forceinline__ void line_ijk(int ln, int s, int& i, int& j, int& k) {
+  const int a = ln % N, b = ln / N;
+  if (D == 0) {
+    i = s; j = a; k = b;
+  } else if (D == 1) {
+    i = a; j = s; k = b;
   } else {
-    s.ptot = s.p;
-    s.Etot = q[4];
-  }
-  return s;
-}
-
-// s . (F, G, H)_inv (Eq. 6); in the perturbation form the difference from the background.
-template <class R>
-__device__ __forceinline__ void flux_inv(const R q[5], const Pt<R>& st, const R s[3], R F[5]) {
-  const R Vn = st.u[0] * s[0] + st.u[1] * s[1] + st.u[2] * s[2];
-  F[0] = q[1] * s[0] + q[2] * s[1] + q[3] * s[2];
-  F[1] = q[1] * Vn + st.p * s[0];
-  F[2] = q[2] * Vn + st.p * s[1];
-  F[3] = q[3] * Vn + st.p * s[2];
-  F[4] = Vn * (st.Etot + st.ptot);
-}
-
-// s . (F, G, H)_v (Eqs. 7-9; energy entry u.tau - f as in Eq. 3).
-// g: the form's grad rho [0..2], grad u [3 + 3a + b] = d u_a / d x_b, the form's grad p [12..14].
-// gr0: background density gradient (perturbation form only).
-template <bool PERT, class R>
-__device__ __forceinline__ void flux_visc(const Pt<R>& st, const R g[15], const R gr0[3], R rho0, R p0,
-                                          const R s[3], const PhysArg<R>& ph, R Fv[5]) {
-  const R mu = st.rho * ph.nu;
-  const R div = g[3] + g[7] + g[11];
-  R ts[3];
-#pragma unroll
-  for (int a = 0; a < 3; ++a) {
-    R acc = R(0);
-#pragma unroll
-    for (int b = 0; b < 3; ++b) acc += (g[3 + 3 * a + b] + g[3 + 3 * b + a]) * s[b];
-    ts[a] = mu * (acc - R(2.0 / 3.0) * div * s[a]);
-  }
-  const R pr = st.ptot / st.rho;
-  R dpr = R(0);
-  if (PERT) dpr = (st.p * rho0 - p0 * st.rhop) / (st.rho * rho0);  // p/rho - p0/rho0
-  R fs = R(0);
-#pragma unroll
-  for (int b = 0; b < 3; ++b) {
-    R A = pr * g[b];
-    if (PERT) A += dpr * gr0[b];
-    const R fb = -ph.CpR * (ph.kappa * (g[12 + b] / ph.gamma - A) + ph.kappa_r * (g[12 + b] - A));
-    fs += fb * s[b];
-  }
-  Fv[0] = R(0);
-  Fv[1] = ts[0];
-  Fv[2] = ts[1];
-  Fv[3] = ts[2];
-  Fv[4] = st.u[0] * ts[0] + st.u[1] * ts[1] + st.u[2] * ts[2] - fs;
-}
-
-// primitive gradients from conserved ones: gq[3 v + n] = d q_v / d x_n
-template <bool PERT, class R>
-__device__ __forceinline__ void grad_prim(const Pt<R>& st, const R gq[15], const R gr0[3], const PhysArg<R>& ph,
-                                          R g[15]) {
-  R grt[3];
-#pragma unroll
-  for (int n = 0; n < 3; ++n) {
-    grt[n] = PERT ? gr0[n] + gq[n] : gq[n];
-    g[n] = gq[n];
-  }
-  const R ir = R(1) / st.rho;
-#pragma unroll
-  for (int a = 0; a < 3; ++a)
-#pragma unroll
-    for (int n = 0; n < 3; ++n) g[3 + 3 * a + n] = (gq[3 * (1 + a) + n] - st.u[a] * grt[n]) * ir;
-  const R ke = R(0.5) * (st.u[0] * st.u[0] + st.u[1] * st.u[1] + st.u[2] * st.u[2]);
-#pragma unroll
-  for (int n = 0; n < 3; ++n)
-    g[12 + n] = ph.gm1 * (gq[12 + n] - (st.u[0] * gq[3 + n] + st.u[1] * gq[6 + n] + st.u[2] * gq[9 + n]) +
-                          ke * grt[n]);
-}
-
-template <bool PERT, class R>
-__device__ __forceinline__ void rusanov(const R qL[5], const Pt<R>& sL, R rho0L, R E0L, const R qR[5],
-                                        const Pt<R>& sR, R rho0R, R E0R, const R n[3], const PhysArg<R>& ph,
-                                        R F[5]) {
-  R FL[5], FR[5];
-  flux_inv(qL, sL, n, FL);
-  flux_inv(qR, sR, n, FR);
-  const R cL = sqrt(ph.gamma * sL.ptot / sL.rho);
-  const R cR = sqrt(ph.gamma * sR.ptot / sR.rho);
-  const R vL = fabs(sL.u[0] * n[0] + sL.u[1] * n[1] + sL.u[2] * n[2]) + cL;
-  const R vR = fabs(sR.u[0] * n[0] + sR.u[1] * n[1] + sR.u[2] * n[2]) + cR;
-  const R lam = vL > vR ? vL : vR;
-#pragma unroll
-  for (int v = 0; v < 5; ++v) F[v] = R(0.5) * (FL[v] + FR[v]) - R(0.5) * lam * (qR[v] - qL[v]);
-  if (PERT) {
-    const R c0L = sqrt(ph.gamma * ph.gm1 * E0L / rho0L);
-    const R c0R = sqrt(ph.gamma * ph.gm1 * E0R / rho0R);
-    const R lam0 = c0L > c0R ? c0L : c0R;
-    F[0] -= R(0.5) * (lam - lam0) * (rho0R - rho0L);
-    F[4] -= R(0.5) * (lam - lam0) * (E0R - E0L);
+    i = a; j = b; k = s;
   }
 }
 
-// ------------------------------------------------------------------ shared layouts
+template <int N, int D>
+__device__ __forceinline__ int line_pt(int ln, int s) {
+  int i, j, k;
+  line_ijk<N, D>(ln, s, i, j, k);
+  return i + N * j + N * N * k;
+}
+
+template <int N, int D, class R>
+__device__ __forceinline__ int line_sidx(int ln, int s) {
+  int i, j, k;
+  line_ijk<N, D>(ln, s, i, j, k);
+  return sidx<N, R>(i, j, k);
+}
 
 template <int N, bool PERT, class R, int EPB>
 struct Layout {
   static constexpr int N2 = N * N, N3 = N * N * N;
-  // per-element sizes in R words
-  static constexpr int SQ = 5 * N3;
-  static constexpr int SG = 15 * N3;
-  static constexpr int SDIV = 5 * N3;
-  static constexpr int ST = 6 * 5 * N2;
-  static constexpr int STV = 6 * 4 * N2;
-  static constexpr int SBG = PERT ? 2 * N3 : 0;
-  static constexpr int SGR0 = PERT ? 3 * N3 : 0;
-  static constexpr int STBG = PERT ? 6 * 2 * N2 : 0;
-  // offsets of the per-CTA arrays (arrays of EPB element blocks), kept 16-byte aligned
-  static constexpr int al(int x) { return (x + (16 / (int)sizeof(R)) - 1) / (16 / (int)sizeof(R)) * (16 / (int)sizeof(R)); }
-  static constexpr int oQ = 0;
-  static constexpr int oBG = oQ + al(EPB * SQ);
-  static constexpr int oGR0 = oBG + al(EPB * SBG);
-  static constexpr int oG = oGR0 + al(EPB * SGR0);
-  static constexpr int oT = oG + al(EPB * SG);
-  static constexpr int oTBG = oT + al(EPB * ST);
-  static constexpr int oTV = oTBG + al(EPB * STBG);
-  static constexpr int oDIV = oTV + al(EPB * STV);
-  static constexpr int total_grad = oTV;  // grad kernel needs no Tv / div
-  static constexpr int total_resid = oDIV + al(EPB * SDIV);
+  static constexpr int SQ = pad_stride<R>(5 * N3);
+  static constexpr int SBG = PERT ? pad_stride<R>(2 * N3) : 0;
+  static constexpr int SGR0 = PERT ? pad_stride<R>(3 * N3) : 0;
+  static constexpr int SG = pad_stride<R>(15 * N3);
+  static constexpr int SDIV = pad_stride<R>(5 * N3);
+  // interpolation I[f][s] and derivative D[i][f] tables, indexed at run time by rolled loops
+  static constexpr int TAB = pad_stride<R>(2 * (N + 1) * N);
+  static constexpr int oTAB = 0;
+  static constexpr int oQ = oTAB + TAB;
+  static constexpr int oBG = oQ + EPB * SQ;
+  static constexpr int oGR0 = oBG + EPB * SBG;
+  static constexpr int oG = oGR0 + EPB * SGR0;
+  static constexpr int oDIV = oG + EPB * SG;
+  static constexpr int total_grad = oDIV;
+  static constexpr int total_resid = oDIV + EPB * SDIV;
+  // per-element bulk copies need 16-byte element blocks in global memory
+  static constexpr bool tmaQ = (5 * N3 * sizeof(R)) % 16 == 0;
+  static constexpr bool tmaBG = (2 * N3 * sizeof(R)) % 16 == 0 && (3 * N3 * sizeof(R)) % 16 == 0;
 };
 
-// Copy `count` R words from global to shared: one bulk TMA copy when aligned, else a cooperative
-// plain copy.  Returns whether the TMA path was used (the caller then waits on the barrier).
-template <class R>
-__device__ __forceinline__ bool stage(R* dst, const R* src, int count, uint64_t* bar, bool issue_tma) {
-  const uint32_t bytes = (uint32_t)count * sizeof(R);
-  const bool tma = issue_tma && (((uintptr_t)src & 15u) == 0) && ((bytes & 15u) == 0) && bytes > 0;
-  if (!tma) {
-    for (int i = threadIdx.x; i < count; i += blockDim.x) dst[i] = src[i];
+// Copy the operator tables into shared memory (static indices only; thread 0).
+template <int N, class R>
+__device__ __forceinline__ void fill_tables(const OpsArg<R>& ops, R* tab) {
+  if (threadIdx.x == 0) {
+#pragma unroll
+    for (int f = 0; f <= N; ++f)
+#pragma unroll
+      for (int s = 0; s < N; ++s) tab[f * N + s] = ops.I[f][s];
+#pragma unroll
+    for (int i = 0; i < N; ++i)
+#pragma unroll
+      for (int f = 0; f <= N; ++f) tab[(N + 1) * N + i * (N + 1) + f] = ops.D[i][f];
   }
-  return tma;
+}
+
+// Load the N values of one component along line ln of direction D from a linear element array.
+template <int N, int D, class R>
+__device__ __forceinline__ void load_line_lin(const R* __restrict__ base, int ln, R out[N]) {
+  if (D == 0 && N == 4 && sizeof(R) == 4) {
+    const float4 v = *reinterpret_cast<const float4*>(base + 4 * ln);
+    out[0] = v.x;
+    out[1] = v.y;
+    out[2] = v.z;
+    out[3] = v.w;
+  } else {
+#pragma unroll
+    for (int s = 0; s < N; ++s) out[s] = base[line_pt<N, D>(ln, s)];
+  }
 }
 
 // ------------------------------------------------------------------ kernel arguments
@@ -265,10 +130,45 @@ struct KArgs {
   R* grad_rho_out;     // optional grad kernel output: lifted d rho / d x_n [E][3][N3]
   R* out;              // residual or new state
   R* T_out;            // traces of the new state (RK mode)
-  const R* un;         // u^n for the RK combination
-  R a, b, dt;          // out = a un + b (q + dt R)
+  const R* un;         // first extra state of the RK combination
+  R a, b, c, dt;       // out = a un + b q + c dt R
+  const R* un2;        // optional second output: out2 = a2 un2 + b2 q + c2 dt R
+  R* out2;
+  R a2, b2, c2;
   unsigned* err;
 };
+
+// neighbour data of one face point
+template <class R>
+struct NbFace {
+  int kind;  // >= 0 interior, -1 inner wall, -2 outer wall
+  R q[5];
+  R tv[4];
+  R r0, E0;
+};
+
+template <int N, bool PERT, bool WANT_TV, class R>
+__device__ __forceinline__ NbFace<R> load_nb(const KArgs<R>& A, int e, int F, int ln) {
+  constexpr int N2 = N * N;
+  NbFace<R> f;
+  f.kind = A.m.nbr[e * 6 + F];
+  if (f.kind >= 0) {
+    const int c = A.m.code[e * 6 + F];
+    const int tp = map_face_pt<N>(ln, c & 7);
+    const size_t base = (size_t)f.kind * 6 + (c >> 3);
+#pragma unroll
+    for (int v = 0; v < 5; ++v) f.q[v] = A.T[(base * 5 + v) * N2 + tp];
+    if (WANT_TV) {
+#pragma unroll
+      for (int v = 0; v < 4; ++v) f.tv[v] = A.Tv[(base * 4 + v) * N2 + tp];
+      if (PERT) {
+        f.r0 = (R)A.bg.bgT[(base * 2) * N2 + tp];
+        f.E0 = (R)A.bg.bgT[(base * 2 + 1) * N2 + tp];
+      }
+    }
+  }
+  return f;
+}
 
 // ------------------------------------------------------------------ trace kernel
 
@@ -288,7 +188,8 @@ __global__ void __launch_bounds__(EPB * N * N) k_trace(const MeshArg<R> m, const
       R lo = R(0), hi = R(0);
 #pragma unroll
       for (int s = 0; s < N; ++s) {
-        const R val = qe[v * N3 + pt_of<N>(d, ln, s)];
+        const int pt = d == 0 ? line_pt<N, 0>(ln, s) : (d == 1 ? line_pt<N, 1>(ln, s) : line_pt<N, 2>(ln, s));
+        const R val = qe[v * N3 + pt];
         lo += ops.I[0][s] * val;
         hi += ops.I[N][s] * val;
       }
@@ -297,212 +198,273 @@ __global__ void __launch_bounds__(EPB * N * N) k_trace(const MeshArg<R> m, const
     }
 }
 
-// ------------------------------------------------------------------ shared lifting phase
+// ------------------------------------------------------------------ staging
 
-// Stages the element data, gathers the neighbour traces and computes the lifted primitive
-// gradients g[15][N3] of every element of the CTA into shared memory (BR1-like averaging,
-// conserved-variable lifting, chain rule with grad xi = S / |J|).
-template <int N, bool PERT, class R, int EPB, bool RESID>
-__device__ __forceinline__ void lift_phase(const KArgs<R>& A, R* sm, uint64_t* bar, int el, int ln, int e,
-                                           bool active, int ne) {
+template <int N, bool PERT, class R, int EPB>
+__device__ __forceinline__ void stage_elements(const KArgs<R>& A, R* sm, uint64_t* bar, int ne) {
+  using L = Layout<N, PERT, R, EPB>;
+  constexpr int N3 = N * N * N;
+  const int e0 = blockIdx.x * EPB;
+  const bool tq = L::tmaQ && (((uintptr_t)A.q & 15u) == 0);
+  const bool tb = PERT && L::tmaBG && (((uintptr_t)A.bg.bg & 15u) == 0) && (((uintptr_t)A.bg.grho0 & 15u) == 0);
+  if (threadIdx.x == 0 && (tq || tb)) {
+    uint32_t bytes = 0;
+    if (tq) bytes += ne * 5 * N3 * sizeof(R);
+    if (tb) bytes += ne * 5 * N3 * sizeof(R);
+    mbar_expect_tx(bar, bytes);
+    for (int el = 0; el < ne; ++el) {
+      if (tq) bulk_g2s(sm + L::oQ + el * L::SQ, A.q + (size_t)(e0 + el) * 5 * N3, 5 * N3 * sizeof(R), bar);
+      if (tb) {
+        bulk_g2s(sm + L::oBG + el * L::SBG, (const R*)A.bg.bg + (size_t)(e0 + el) * 2 * N3, 2 * N3 * sizeof(R), bar);
+        bulk_g2s(sm + L::oGR0 + el * L::SGR0, (const R*)A.bg.grho0 + (size_t)(e0 + el) * 3 * N3, 3 * N3 * sizeof(R),
+                 bar);
+      }
+    }
+  }
+  if (!tq) {
+    for (int i = threadIdx.x; i < ne * 5 * N3; i += blockDim.x)
+      sm[L::oQ + (i / (5 * N3)) * L::SQ + i % (5 * N3)] = A.q[(size_t)e0 * 5 * N3 + i];
+  }
+  if (PERT && !tb) {
+    for (int i = threadIdx.x; i < ne * 2 * N3; i += blockDim.x)
+      sm[L::oBG + (i / (2 * N3)) * L::SBG + i % (2 * N3)] = (R)A.bg.bg[(size_t)e0 * 2 * N3 + i];
+    for (int i = threadIdx.x; i < ne * 3 * N3; i += blockDim.x)
+      sm[L::oGR0 + (i / (3 * N3)) * L::SGR0 + i % (3 * N3)] = (R)A.bg.grho0[(size_t)e0 * 3 * N3 + i];
+  }
+  if (tq || tb) mbar_wait0(bar, A.err);
+}
+
+// ------------------------------------------------------------------ lifting, one direction
+
+// d q / d xi_D along the thread's D-line with common face values (BR1-like averaging, Section 3;
+// walls Section 5), times grad xi_D = S^D / |J|, accumulated into the gradient array.
+template <int N, bool PERT, class R, int EPB, int D>
+__device__ __forceinline__ void lift_dir(const KArgs<R>& A, R* sm, int el, int ln, int e) {
   using L = Layout<N, PERT, R, EPB>;
   constexpr int N2 = N * N, N3 = N * N * N;
-  const int e0 = blockIdx.x * EPB;
-  R* sq = sm + L::oQ;
-  R* sbg = sm + L::oBG;
-  R* sgr0 = sm + L::oGR0;
-  R* sg = sm + L::oG;
-  R* sT = sm + L::oT;
-  R* sTbg = sm + L::oTBG;
-  R* sTv = sm + L::oTV;
+  const R* sq = sm + L::oQ + el * L::SQ;
+  const R* sbg = sm + L::oBG + el * L::SBG;
+  R* sg = sm + L::oG + el * L::SG;
+  const PhysArg<R>& ph = A.ph;
 
-  // ---- stage the element blocks (bulk TMA when aligned)
-  const bool full = (ne == EPB);
-  bool t0 = stage(sq, A.q + (size_t)e0 * 5 * N3, ne * 5 * N3, bar, full);
-  bool t1 = false, t2 = false;
+  R qv[5][N];
+#pragma unroll
+  for (int v = 0; v < 5; ++v) load_line_lin<N, D>(sq + v * N3, ln, qv[v]);
+  R r0[N], E0l[N];
   if (PERT) {
-    t1 = stage(sbg, (const R*)A.bg.bg + (size_t)e0 * 2 * N3, ne * 2 * N3, bar, full);
-    t2 = stage(sgr0, (const R*)A.bg.grho0 + (size_t)e0 * 3 * N3, ne * 3 * N3, bar, full);
+    load_line_lin<N, D>(sbg, ln, r0);
+    load_line_lin<N, D>(sbg + N3, ln, E0l);
   }
-  if (threadIdx.x == 0 && (t0 || t1 || t2)) {
-    uint32_t bytes = (t0 ? ne * 5 * N3 : 0) * sizeof(R);
-    if (PERT) bytes += ((t1 ? ne * 2 * N3 : 0) + (t2 ? ne * 3 * N3 : 0)) * sizeof(R);
-    mbar_expect_tx(bar, bytes);
-    if (t0) bulk_g2s(sq, A.q + (size_t)e0 * 5 * N3, ne * 5 * N3 * sizeof(R), bar);
-    if (PERT && t1) bulk_g2s(sbg, (const R*)A.bg.bg + (size_t)e0 * 2 * N3, ne * 2 * N3 * sizeof(R), bar);
-    if (PERT && t2) bulk_g2s(sgr0, (const R*)A.bg.grho0 + (size_t)e0 * 3 * N3, ne * 3 * N3 * sizeof(R), bar);
-  }
+  R S[3][N + 1];
+  const R* Sl = A.m.Sf + ((size_t)e * 3 + D) * 3 * (N + 1) * N2;
+#pragma unroll
+  for (int n = 0; n < 3; ++n)
+#pragma unroll
+    for (int f = 0; f <= N; ++f) S[n][f] = __ldg(Sl + (n * (N + 1) + f) * N2 + ln);
 
-  // ---- gather neighbour face data (overlaps the bulk copy) and clear the gradient accumulator
-  if (active) {
-#pragma unroll 1
-    for (int F = 0; F < 6; ++F) {
-      const int nb = A.m.nbr[e * 6 + F];
-      if (nb >= 0) {
-        const int c = A.m.code[e * 6 + F];
-        const int tp = map_face_pt<N>(ln, c & 7);
-        const size_t base = (size_t)nb * 6 + (c >> 3);
+  R dq[5][2];  // common state minus own trace at the two ends
 #pragma unroll
-        for (int v = 0; v < 5; ++v) sT[(el * 6 + F) * 5 * N2 + v * N2 + ln] = A.T[base * 5 * N2 + v * N2 + tp];
-        if (RESID) {
+  for (int side = 0; side < 2; ++side) {
+    const int f = side ? N : 0;
+    const int F = 2 * D + side;
+    const NbFace<R> nb = load_nb<N, PERT, false>(A, e, F, ln);
+    R qe[5];
 #pragma unroll
-          for (int v = 0; v < 4; ++v) sTv[(el * 6 + F) * 4 * N2 + v * N2 + ln] = A.Tv[base * 4 * N2 + v * N2 + tp];
-          if (PERT) {
+    for (int v = 0; v < 5; ++v) {
+      R acc = R(0);
 #pragma unroll
-            for (int v = 0; v < 2; ++v)
-              sTbg[(el * 6 + F) * 2 * N2 + v * N2 + ln] = (R)A.bg.bgT[base * 2 * N2 + v * N2 + tp];
-          }
-        }
-      }
+      for (int s = 0; s < N; ++s) acc += A.ops.I[f][s] * qv[v][s];
+      qe[v] = acc;
     }
-  }
-  for (int i = threadIdx.x; i < EPB * 15 * N3; i += blockDim.x) sg[i] = R(0);
-  if (t0 || t1 || t2) mbar_wait0(bar, A.err);
-  __syncthreads();
-
-  // ---- lifting, one direction at a time
-#pragma unroll 1
-  for (int d = 0; d < 3; ++d) {
-    if (active) {
-      R qv[5][N];
-      R r0[N], E0l[N];
+    if (nb.kind >= 0) {
 #pragma unroll
-      for (int s = 0; s < N; ++s) {
-        const int pt = pt_of<N>(d, ln, s);
-#pragma unroll
-        for (int v = 0; v < 5; ++v) qv[v][s] = sq[el * 5 * N3 + v * N3 + pt];
-        if (PERT) {
-          r0[s] = sbg[el * 2 * N3 + pt];
-          E0l[s] = sbg[el * 2 * N3 + N3 + pt];
-        } else {
-          r0[s] = R(0);
-          E0l[s] = R(0);
-        }
-      }
-      R S[3][N + 1];
-      const R* Sl = A.m.Sf + ((size_t)e * 3 + d) * 3 * (N + 1) * N2;
-#pragma unroll
-      for (int n = 0; n < 3; ++n)
-#pragma unroll
-        for (int f = 0; f <= N; ++f) S[n][f] = Sl[(n * (N + 1) + f) * N2 + ln];
-      // common state at both ends
-      R dq[5][2];  // q_c - q_own at end 0 and end N
-#pragma unroll
-      for (int side = 0; side < 2; ++side) {
-        const int f = side ? N : 0;
-        const int F = 2 * d + side;
-        R qe[5];
-        R rho0e = R(0), E0e = R(0);
-#pragma unroll
-        for (int v = 0; v < 5; ++v) {
-          R acc = R(0);
-#pragma unroll
-          for (int s = 0; s < N; ++s) acc += A.ops.I[f][s] * qv[v][s];
-          qe[v] = acc;
-        }
-        if (PERT) {
-#pragma unroll
-          for (int s = 0; s < N; ++s) {
-            rho0e += A.ops.I[f][s] * r0[s];
-            E0e += A.ops.I[f][s] * E0l[s];
-          }
-        }
-        const int nb = A.m.nbr[e * 6 + F];
-        if (nb >= 0) {
-#pragma unroll
-          for (int v = 0; v < 5; ++v)
-            dq[v][side] = R(0.5) * (sT[(el * 6 + F) * 5 * N2 + v * N2 + ln] - qe[v]);
-        } else {
-          // wall common state: zero normal velocity, interior density, interior pressure (inner
-          // wall) or p = R rho T_top (outer wall)
-          const R sg_ = side ? R(1) : R(-1);
-          const R mag = sqrt(S[0][f] * S[0][f] + S[1][f] * S[1][f] + S[2][f] * S[2][f]);
-          const R nh[3] = {sg_ * S[0][f] / mag, sg_ * S[1][f] / mag, sg_ * S[2][f] / mag};
-          const Pt<R> st = point_state<PERT>(qe, rho0e, E0e, A.ph);
-          const R mn = qe[1] * nh[0] + qe[2] * nh[1] + qe[3] * nh[2];
-          R mc[3] = {qe[1] - mn * nh[0], qe[2] - mn * nh[1], qe[3] - mn * nh[2]};
-          R pc;
-          if (nb == -2) pc = A.ph.Rgas * st.rhop * A.ph.T_top;  // the form's density times R T_top
-          else pc = st.p;
-          const R Ec = pc / A.ph.gm1 + R(0.5) * (mc[0] * mc[0] + mc[1] * mc[1] + mc[2] * mc[2]) / st.rho;
-          dq[0][side] = R(0);
-          dq[1][side] = mc[0] - qe[1];
-          dq[2][side] = mc[1] - qe[2];
-          dq[3][side] = mc[2] - qe[3];
-          dq[4][side] = Ec - qe[4];
-        }
-      }
-      // grad xi_d at the line's solution points
-      R gx[3][N];
-#pragma unroll
-      for (int i = 0; i < N; ++i) {
-        const R ij = A.m.invJ[(size_t)e * N3 + pt_of<N>(d, ln, i)];
-#pragma unroll
-        for (int n = 0; n < 3; ++n) {
-          R acc = R(0);
-#pragma unroll
-          for (int f = 0; f <= N; ++f) acc += A.ops.Lfs[i][f] * S[n][f];
-          gx[n][i] = acc * ij;
-        }
-      }
-      // d q / d xi_d = Dsol q + D[:,0] (q_c0 - q_0) + D[:,N] (q_cN - q_N), then accumulate grad q
-#pragma unroll
-      for (int i = 0; i < N; ++i) {
-        const int pt = pt_of<N>(d, ln, i);
-#pragma unroll
-        for (int v = 0; v < 5; ++v) {
-          R acc = A.ops.D[i][0] * dq[v][0] + A.ops.D[i][N] * dq[v][1];
-#pragma unroll
-          for (int s = 0; s < N; ++s) acc += A.ops.Dsol[i][s] * qv[v][s];
-#pragma unroll
-          for (int n = 0; n < 3; ++n) sg[el * 15 * N3 + (3 * v + n) * N3 + pt] += acc * gx[n][i];
-        }
-      }
-    }
-    __syncthreads();
-  }
-
-  // ---- optional raw density-gradient output, then conversion to primitive gradients
-  if (active) {
-#pragma unroll 1
-    for (int i = 0; i < N; ++i) {
-      const int pt = N * ln + i;
-      if (A.grad_rho_out) {
-#pragma unroll
-        for (int n = 0; n < 3; ++n) A.grad_rho_out[((size_t)e * 3 + n) * N3 + pt] = sg[el * 15 * N3 + n * N3 + pt];
-      }
-      R q[5], gq[15], gr0[3], g[15];
-#pragma unroll
-      for (int v = 0; v < 5; ++v) q[v] = sq[el * 5 * N3 + v * N3 + pt];
-#pragma unroll
-      for (int c = 0; c < 15; ++c) gq[c] = sg[el * 15 * N3 + c * N3 + pt];
-      R rho0 = R(0), E0 = R(0);
+      for (int v = 0; v < 5; ++v) dq[v][side] = R(0.5) * (nb.q[v] - qe[v]);
+    } else {
+      R rho0e = R(0), E0e = R(0);
       if (PERT) {
-        rho0 = sbg[el * 2 * N3 + pt];
-        E0 = sbg[el * 2 * N3 + N3 + pt];
 #pragma unroll
-        for (int n = 0; n < 3; ++n) gr0[n] = sgr0[el * 3 * N3 + n * N3 + pt];
-      } else {
-        gr0[0] = gr0[1] = gr0[2] = R(0);
+        for (int s = 0; s < N; ++s) {
+          rho0e += A.ops.I[f][s] * r0[s];
+          E0e += A.ops.I[f][s] * E0l[s];
+        }
       }
-      const Pt<R> st = point_state<PERT>(q, rho0, E0, A.ph);
+      // wall common state: zero normal velocity, interior density, interior pressure (inner wall)
+      // or p = R rho T_top (outer wall)
+      const R sg_ = side ? R(1) : R(-1);
+      const R mag = sqrt(S[0][f] * S[0][f] + S[1][f] * S[1][f] + S[2][f] * S[2][f]);
+      const R nh[3] = {sg_ * S[0][f] / mag, sg_ * S[1][f] / mag, sg_ * S[2][f] / mag};
+      const Pt<R> st = point_state<PERT>(qe, rho0e, E0e, ph);
+      const R mn = qe[1] * nh[0] + qe[2] * nh[1] + qe[3] * nh[2];
+      const R mc[3] = {qe[1] - mn * nh[0], qe[2] - mn * nh[1], qe[3] - mn * nh[2]};
+      const R pc = nb.kind == -2 ? ph.Rgas * st.rhop * ph.T_top : st.p;
+      const R Ec = pc / ph.gm1 + R(0.5) * (mc[0] * mc[0] + mc[1] * mc[1] + mc[2] * mc[2]) / st.rho;
+      dq[0][side] = R(0);
+      dq[1][side] = mc[0] - qe[1];
+      dq[2][side] = mc[1] - qe[2];
+      dq[3][side] = mc[2] - qe[3];
+      dq[4][side] = Ec - qe[4];
+    }
+  }
+#pragma unroll
+  for (int i = 0; i < N; ++i) {
+    const R ij = __ldg(A.m.invJ + (size_t)e * N3 + line_pt<N, D>(ln, i));
+    R gx[3];
+#pragma unroll
+    for (int n = 0; n < 3; ++n) {
+      R acc = R(0);
+#pragma unroll
+      for (int f = 0; f <= N; ++f) acc += A.ops.Lfs[i][f] * S[n][f];
+      gx[n] = acc * ij;
+    }
+    const int si = line_sidx<N, D, R>(ln, i);
+#pragma unroll
+    for (int v = 0; v < 5; ++v) {
+      R dv = A.ops.D[i][0] * dq[v][0] + A.ops.D[i][N] * dq[v][1];
+#pragma unroll
+      for (int s = 0; s < N; ++s) dv += A.ops.Dsol[i][s] * qv[v][s];
+#pragma unroll
+      for (int n = 0; n < 3; ++n) {
+        R* p = sg + (3 * v + n) * N3 + si;
+        if (D == 0) *p = dv * gx[n];
+        else *p += dv * gx[n];
+      }
+    }
+  }
+}
+
+// Lifting of every element of the CTA; afterwards the first kG component arrays of the gradient
+// array hold the gradient record (grad rho, trace-free strain, grad p) of the form's variables.
+template <int N, bool PERT, class R, int EPB>
+__device__ __forceinline__ void lift_all(const KArgs<R>& A, R* sm, int el, int ln, int e, bool active) {
+  using L = Layout<N, PERT, R, EPB>;
+  constexpr int N3 = N * N * N;
+  if (active) lift_dir<N, PERT, R, EPB, 0>(A, sm, el, ln, e);
+  __syncthreads();
+  if (active) lift_dir<N, PERT, R, EPB, 1>(A, sm, el, ln, e);
+  __syncthreads();
+  if (active) lift_dir<N, PERT, R, EPB, 2>(A, sm, el, ln, e);
+  __syncthreads();
+  if (active) {
+    const R* sq = sm + L::oQ + el * L::SQ;
+    const R* sbg = sm + L::oBG + el * L::SBG;
+    const R* sgr0 = sm + L::oGR0 + el * L::SGR0;
+    R* sg = sm + L::oG + el * L::SG;
+    R qv[5][N], r0[N], E0l[N], g0[3][N];
+#pragma unroll
+    for (int v = 0; v < 5; ++v) load_line_lin<N, 0>(sq + v * N3, ln, qv[v]);
+    if (PERT) {
+      load_line_lin<N, 0>(sbg, ln, r0);
+      load_line_lin<N, 0>(sbg + N3, ln, E0l);
+#pragma unroll
+      for (int n = 0; n < 3; ++n) load_line_lin<N, 0>(sgr0 + n * N3, ln, g0[n]);
+    }
+#pragma unroll
+    for (int i = 0; i < N; ++i) {
+      const int si = line_sidx<N, 0, R>(ln, i);
+      R q[5], gq[15], gr0[3], g[kG];
+#pragma unroll
+      for (int v = 0; v < 5; ++v) q[v] = qv[v][i];
+#pragma unroll
+      for (int c = 0; c < 15; ++c) gq[c] = sg[c * N3 + si];
+      if (A.grad_rho_out) {
+        const int pt = line_pt<N, 0>(ln, i);
+#pragma unroll
+        for (int n = 0; n < 3; ++n) A.grad_rho_out[((size_t)e * 3 + n) * N3 + pt] = gq[n];
+      }
+#pragma unroll
+      for (int n = 0; n < 3; ++n) gr0[n] = PERT ? g0[n][i] : R(0);
+      const Pt<R> st = point_state<PERT>(q, PERT ? r0[i] : R(0), PERT ? E0l[i] : R(0), A.ph);
       grad_prim<PERT>(st, gq, gr0, A.ph, g);
 #pragma unroll
-      for (int c = 0; c < 15; ++c) sg[el * 15 * N3 + c * N3 + pt] = g[c];
+      for (int c = 0; c < kG; ++c) sg[c * N3 + si] = g[c];
     }
   }
   __syncthreads();
 }
 
+// Interpolated state, background and gradients of line ln at flux point f of direction D.
+template <int N, bool PERT, class R>
+struct FluxPointData {
+  R q[5], g[kG], gr0[3], r0, E0;
+};
+
 // ------------------------------------------------------------------ gradient kernel
 
 // Lifted gradients, then the one-sided normal viscous flux F_v . n_out on every face point,
 // written for the neighbours: Tv[e][F][0..2] = tau n, Tv[e][F][3] = u.tau n - f.n.
-template <int N, bool PERT, class R, int EPB>
-__global__ void __launch_bounds__(EPB * N * N) k_grad(const KArgs<R> A) {
+template <int N, bool PERT, class R, int EPB, int D>
+__device__ __forceinline__ void face_visc_dir(const KArgs<R>& A, const R* sm, int el, int ln, int e) {
   using L = Layout<N, PERT, R, EPB>;
   constexpr int N2 = N * N, N3 = N * N * N;
-  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const R* sq = sm + L::oQ + el * L::SQ;
+  const R* sbg = sm + L::oBG + el * L::SBG;
+  const R* sgr0 = sm + L::oGR0 + el * L::SGR0;
+  const R* sg = sm + L::oG + el * L::SG;
+  const R* tI = sm + L::oTAB;
+  const R* Sl = A.m.Sf + ((size_t)e * 3 + D) * 3 * (N + 1) * N2;
+  R qv[5][N], gv[kG][N], r0[N], E0l[N], g0[3][N];
+#pragma unroll
+  for (int v = 0; v < 5; ++v) load_line_lin<N, D>(sq + v * N3, ln, qv[v]);
+#pragma unroll
+  for (int s = 0; s < N; ++s) {
+    const int si = line_sidx<N, D, R>(ln, s);
+#pragma unroll
+    for (int c = 0; c < kG; ++c) gv[c][s] = sg[c * N3 + si];
+  }
+  if (PERT) {
+    load_line_lin<N, D>(sbg, ln, r0);
+    load_line_lin<N, D>(sbg + N3, ln, E0l);
+#pragma unroll
+    for (int n = 0; n < 3; ++n) load_line_lin<N, D>(sgr0 + n * N3, ln, g0[n]);
+  }
+#pragma unroll 1
+  for (int side = 0; side < 2; ++side) {
+    const int f = side ? N : 0;
+    R w[N];
+#pragma unroll
+    for (int s = 0; s < N; ++s) w[s] = tI[f * N + s];
+    R qf[5], gf[kG], gr0f[3] = {R(0), R(0), R(0)};
+    R rho0f = R(0), E0f = R(0);
+#pragma unroll
+    for (int v = 0; v < 5; ++v) {
+      qf[v] = R(0);
+#pragma unroll
+      for (int s = 0; s < N; ++s) qf[v] += w[s] * qv[v][s];
+    }
+#pragma unroll
+    for (int c = 0; c < kG; ++c) {
+      gf[c] = R(0);
+#pragma unroll
+      for (int s = 0; s < N; ++s) gf[c] += w[s] * gv[c][s];
+    }
+    if (PERT) {
+#pragma unroll
+      for (int s = 0; s < N; ++s) {
+        rho0f += w[s] * r0[s];
+        E0f += w[s] * E0l[s];
+#pragma unroll
+        for (int n = 0; n < 3; ++n) gr0f[n] += w[s] * g0[n][s];
+      }
+    }
+    R s3[3];
+#pragma unroll
+    for (int n = 0; n < 3; ++n) s3[n] = __ldg(Sl + (n * (N + 1) + f) * N2 + ln);
+    const R sgn = side ? R(1) : R(-1);
+    const R mag = sqrt(s3[0] * s3[0] + s3[1] * s3[1] + s3[2] * s3[2]);
+    const R nh[3] = {sgn * s3[0] / mag, sgn * s3[1] / mag, sgn * s3[2] / mag};
+    const Pt<R> st = point_state<PERT>(qf, rho0f, E0f, A.ph);
+    R Fv[5];
+    flux_visc<PERT>(st, gf, gr0f, rho0f, A.ph.gm1 * E0f, nh, A.ph, Fv);
+    R* o = A.Tv_out + ((size_t)e * 6 + 2 * D + side) * 4 * N2;
+#pragma unroll
+    for (int v = 0; v < 4; ++v) o[v * N2 + ln] = Fv[1 + v];
+  }
+}
+
+template <int N, bool PERT, class R, int EPB>
+__global__ void __launch_bounds__(EPB * N * N) k_grad(const KArgs<R> A) {
+  constexpr int N2 = N * N;
+  extern __shared__ __align__(128) unsigned char smem_raw[];
   __shared__ __align__(8) uint64_t bar;
   R* sm = reinterpret_cast<R*>(smem_raw);
   const int el = threadIdx.x / N2, ln = threadIdx.x % N2;
@@ -511,62 +473,178 @@ __global__ void __launch_bounds__(EPB * N * N) k_grad(const KArgs<R> A) {
   const int e = e0 + el;
   const bool active = el < ne;
   if (threadIdx.x == 0) mbar_init(&bar);
+  fill_tables<N, R>(A.ops, sm + Layout<N, PERT, R, EPB>::oTAB);
   __syncthreads();
-  lift_phase<N, PERT, R, EPB, false>(A, sm, &bar, el, ln, e, active, ne);
+  stage_elements<N, PERT, R, EPB>(A, sm, &bar, ne);
+  __syncthreads();
+  lift_all<N, PERT, R, EPB>(A, sm, el, ln, e, active);
   if (!active || A.Tv_out == nullptr) return;
-  const R* sq = sm + L::oQ;
-  const R* sbg = sm + L::oBG;
-  const R* sgr0 = sm + L::oGR0;
-  const R* sg = sm + L::oG;
-#pragma unroll 1
-  for (int d = 0; d < 3; ++d) {
-    const R* Sl = A.m.Sf + ((size_t)e * 3 + d) * 3 * (N + 1) * N2;
-#pragma unroll 1
-    for (int side = 0; side < 2; ++side) {
-      const int f = side ? N : 0;
-      R qf[5] = {R(0), R(0), R(0), R(0), R(0)}, gf[15], gr0f[3] = {R(0), R(0), R(0)};
-      R rho0f = R(0), E0f = R(0);
+  face_visc_dir<N, PERT, R, EPB, 0>(A, sm, el, ln, e);
+  face_visc_dir<N, PERT, R, EPB, 1>(A, sm, el, ln, e);
+  face_visc_dir<N, PERT, R, EPB, 2>(A, sm, el, ln, e);
+}
+
+// ------------------------------------------------------------------ flux sweep, one direction
+
+// Transformed fluxes at the N+1 flux points of the thread's D-line (Eq. 12), common fluxes at
+// the two ends (Rusanov + averaged viscous; walls per Section 5), derivative back to the solution
+// points (Eq. 18), accumulated into the divergence array.
+template <int N, bool PERT, class R, int EPB, int D>
+__device__ __forceinline__ void flux_dir(const KArgs<R>& A, R* sm, int el, int ln, int e) {
+  using L = Layout<N, PERT, R, EPB>;
+  constexpr int N2 = N * N, N3 = N * N * N;
+  const R* sq = sm + L::oQ + el * L::SQ;
+  const R* sbg = sm + L::oBG + el * L::SBG;
+  const R* sgr0 = sm + L::oGR0 + el * L::SGR0;
+  const R* sg = sm + L::oG + el * L::SG;
+  R* sdiv = sm + L::oDIV + el * L::SDIV;
+  const PhysArg<R>& ph = A.ph;
+
+  // line data in registers (FP32); the FP64 form re-reads the gradients from shared memory per
+  // flux point to stay within the register file
+  constexpr bool kRegGrad = sizeof(R) == 4;
+  R qv[5][N], gv[kRegGrad ? kG : 1][N];
 #pragma unroll
-      for (int c = 0; c < 15; ++c) gf[c] = R(0);
+  for (int v = 0; v < 5; ++v) load_line_lin<N, D>(sq + v * N3, ln, qv[v]);
+  if constexpr (kRegGrad) {
+#pragma unroll
+    for (int s = 0; s < N; ++s) {
+      const int si = line_sidx<N, D, R>(ln, s);
+#pragma unroll
+      for (int c = 0; c < kG; ++c) gv[c][s] = sg[c * N3 + si];
+    }
+  }
+  // the background line is read from shared memory per flux point (register budget)
+  const R* Sl = A.m.Sf + ((size_t)e * 3 + D) * 3 * (N + 1) * N2;
+
+  R acc[5][N];
+#pragma unroll
+  for (int v = 0; v < 5; ++v)
+#pragma unroll
+    for (int i = 0; i < N; ++i) acc[v][i] = R(0);
+  const R* tI = sm + L::oTAB;
+  const R* tD = sm + L::oTAB + (N + 1) * N;
+
+  // one rolled loop over the flux points keeps a single copy of the flux code per direction
+#pragma unroll 1
+  for (int f = 0; f <= N; ++f) {
+    R w[N];
+#pragma unroll
+    for (int s = 0; s < N; ++s) w[s] = tI[f * N + s];
+    FluxPointData<N, PERT, R> P;
+#pragma unroll
+    for (int v = 0; v < 5; ++v) {
+      R t = R(0);
+#pragma unroll
+      for (int s = 0; s < N; ++s) t += w[s] * qv[v][s];
+      P.q[v] = t;
+    }
+#pragma unroll
+    for (int c = 0; c < kG; ++c) {
+      R t = R(0);
 #pragma unroll
       for (int s = 0; s < N; ++s) {
-        const int pt = pt_of<N>(d, ln, s);
-        const R w = A.ops.I[f][s];
-#pragma unroll
-        for (int v = 0; v < 5; ++v) qf[v] += w * sq[el * 5 * N3 + v * N3 + pt];
-#pragma unroll
-        for (int c = 0; c < 15; ++c) gf[c] += w * sg[el * 15 * N3 + c * N3 + pt];
-        if (PERT) {
-          rho0f += w * sbg[el * 2 * N3 + pt];
-          E0f += w * sbg[el * 2 * N3 + N3 + pt];
-#pragma unroll
-          for (int n = 0; n < 3; ++n) gr0f[n] += w * sgr0[el * 3 * N3 + n * N3 + pt];
-        }
+        if constexpr (kRegGrad) t += w[s] * gv[c][s];
+        else t += w[s] * sg[c * N3 + line_sidx<N, D, R>(ln, s)];
       }
-      R s3[3];
+      P.g[c] = t;
+    }
+    P.r0 = R(0);
+    P.E0 = R(0);
 #pragma unroll
-      for (int n = 0; n < 3; ++n) s3[n] = Sl[(n * (N + 1) + f) * N2 + ln];
+    for (int n = 0; n < 3; ++n) P.gr0[n] = R(0);
+    if (PERT) {
+#pragma unroll
+      for (int s = 0; s < N; ++s) {
+        const int pt = line_pt<N, D>(ln, s);
+        P.r0 += w[s] * sbg[pt];
+        P.E0 += w[s] * sbg[N3 + pt];
+#pragma unroll
+        for (int n = 0; n < 3; ++n) P.gr0[n] += w[s] * sgr0[n * N3 + pt];
+      }
+    }
+    R s3[3];
+#pragma unroll
+    for (int n = 0; n < 3; ++n) s3[n] = __ldg(Sl + (n * (N + 1) + f) * N2 + ln);
+    const Pt<R> st = point_state<PERT>(P.q, P.r0, P.E0, ph);
+    const R p0f = ph.gm1 * P.E0;
+    R Ft[5];
+    if (f > 0 && f < N) {
+      R Fi[5], Fv[5];
+      flux_inv(P.q, st, s3, Fi);
+      flux_visc<PERT>(st, P.g, P.gr0, P.r0, p0f, s3, ph, Fv);
+#pragma unroll
+      for (int v = 0; v < 5; ++v) Ft[v] = Fi[v] - Fv[v];
+    } else {
+      const int side = (f == N);
+      const int F = 2 * D + side;
+      const NbFace<R> nb = load_nb<N, PERT, true>(A, e, F, ln);
       const R sgn = side ? R(1) : R(-1);
       const R mag = sqrt(s3[0] * s3[0] + s3[1] * s3[1] + s3[2] * s3[2]);
       const R nh[3] = {sgn * s3[0] / mag, sgn * s3[1] / mag, sgn * s3[2] / mag};
-      const Pt<R> st = point_state<PERT>(qf, rho0f, E0f, A.ph);
-      R Fv[5];
-      flux_visc<PERT>(st, gf, gr0f, rho0f, A.ph.gm1 * E0f, nh, A.ph, Fv);
-      const int F = 2 * d + side;
-      R* o = A.Tv_out + ((size_t)e * 6 + F) * 4 * N2;
+      R Fh[5];
+      if (nb.kind >= 0) {
+        const Pt<R> sR = point_state<PERT>(nb.q, nb.r0, nb.E0, ph);
+        rusanov<PERT>(P.q, st, P.r0, P.E0, nb.q, sR, nb.r0, nb.E0, nh, ph, Fh);
+        R Fv[5];
+        flux_visc<PERT>(st, P.g, P.gr0, P.r0, p0f, nh, ph, Fv);
 #pragma unroll
-      for (int v = 0; v < 4; ++v) o[v * N2 + ln] = Fv[1 + v];
+        for (int v = 1; v < 5; ++v)  // the neighbour stored F_v . n_out(neighbour) = -F_v . n
+          Fh[v] -= R(0.5) * (Fv[v] - nb.tv[v - 1]);
+      } else {
+        // walls (Section 5): exact inviscid flux (0, p n, 0); normal traction only;
+        // energy: f.n from the lifted gradient with T = T_top (outer) or the prescribed flux (inner)
+        const R mu = st.rho * ph.nu;
+        R trac = R(0);
+#pragma unroll
+        for (int a = 0; a < 3; ++a)
+#pragma unroll
+          for (int b = 0; b < 3; ++b) trac += nh[a] * mu * sig(P.g, a, b) * nh[b];
+        Fh[0] = R(0);
+#pragma unroll
+        for (int a = 0; a < 3; ++a) Fh[1 + a] = (st.p - trac) * nh[a];
+        if (nb.kind == -2) {
+          const R RT = ph.Rgas * ph.T_top;
+          R fn = R(0);
+#pragma unroll
+          for (int b = 0; b < 3; ++b)
+            fn += -ph.CpR *
+                  (ph.kappa * (P.g[9 + b] / ph.gamma - RT * P.g[b]) + ph.kappa_r * (P.g[9 + b] - RT * P.g[b])) *
+                  nh[b];
+          Fh[4] = fn;
+        } else {
+          Fh[4] = PERT ? R(0) : -ph.bottom_flux;
+        }
+      }
+#pragma unroll
+      for (int v = 0; v < 5; ++v) Ft[v] = sgn * mag * Fh[v];
+    }
+#pragma unroll
+    for (int i = 0; i < N; ++i) {
+      const R dc = tD[i * (N + 1) + f];
+#pragma unroll
+      for (int v = 0; v < 5; ++v) acc[v][i] += dc * Ft[v];
+    }
+  }
+#pragma unroll
+  for (int i = 0; i < N; ++i) {
+    const int si = line_sidx<N, D, R>(ln, i);
+#pragma unroll
+    for (int v = 0; v < 5; ++v) {
+      if (D == 0) sdiv[v * N3 + si] = acc[v][i];
+      else sdiv[v * N3 + si] += acc[v][i];
     }
   }
 }
 
 // ------------------------------------------------------------------ residual kernel
 
+// FP32: ask for three resident CTAs per SM (register cap ~168 per thread)
 template <int N, bool PERT, class R, int EPB, int MODE>
-__global__ void __launch_bounds__(EPB * N * N) k_resid(const KArgs<R> A) {
+__global__ void __launch_bounds__(EPB * N * N, sizeof(R) == 4 ? 3 : 1) k_resid(const KArgs<R> A) {
   using L = Layout<N, PERT, R, EPB>;
   constexpr int N2 = N * N, N3 = N * N * N;
-  extern __shared__ __align__(16) unsigned char smem_raw[];
+  extern __shared__ __align__(128) unsigned char smem_raw[];
   __shared__ __align__(8) uint64_t bar;
   R* sm = reinterpret_cast<R*>(smem_raw);
   const int el = threadIdx.x / N2, ln = threadIdx.x % N2;
@@ -575,150 +653,34 @@ __global__ void __launch_bounds__(EPB * N * N) k_resid(const KArgs<R> A) {
   const int e = e0 + el;
   const bool active = el < ne;
   if (threadIdx.x == 0) mbar_init(&bar);
+  fill_tables<N, R>(A.ops, sm + Layout<N, PERT, R, EPB>::oTAB);
   __syncthreads();
-  lift_phase<N, PERT, R, EPB, true>(A, sm, &bar, el, ln, e, active, ne);
-  R* sq = sm + L::oQ;
-  const R* sbg = sm + L::oBG;
-  const R* sgr0 = sm + L::oGR0;
-  const R* sg = sm + L::oG;
-  const R* sT = sm + L::oT;
-  const R* sTbg = sm + L::oTBG;
-  const R* sTv = sm + L::oTV;
-  R* sdiv = sm + L::oDIV;
+  stage_elements<N, PERT, R, EPB>(A, sm, &bar, ne);
+  __syncthreads();
+  lift_all<N, PERT, R, EPB>(A, sm, el, ln, e, active);
+  if (active) flux_dir<N, PERT, R, EPB, 0>(A, sm, el, ln, e);
+  __syncthreads();
+  if (active) flux_dir<N, PERT, R, EPB, 1>(A, sm, el, ln, e);
+  __syncthreads();
+  if (active) flux_dir<N, PERT, R, EPB, 2>(A, sm, el, ln, e);
+  __syncthreads();
+
+  // residual dQ/dt = -div/|J| - M (Eqs. 4, 11), sources of Eqs. 2-3, and the RK combination
+  R* sq = sm + L::oQ + el * L::SQ;
+  const R* sdiv = sm + L::oDIV + el * L::SDIV;
   const PhysArg<R>& ph = A.ph;
-
-  // ---- flux sweeps: transformed fluxes at the flux points, common fluxes at the two ends,
-  //      derivative back to the solution points (Eqs. 12, 17, 18)
-#pragma unroll 1
-  for (int d = 0; d < 3; ++d) {
-    if (active) {
-      R acc[5][N];
-#pragma unroll
-      for (int v = 0; v < 5; ++v)
-#pragma unroll
-        for (int i = 0; i < N; ++i) acc[v][i] = R(0);
-      const R* Sl = A.m.Sf + ((size_t)e * 3 + d) * 3 * (N + 1) * N2;
-#pragma unroll
-      for (int f = 0; f <= N; ++f) {
-        R qf[5], gf[15], gr0f[3] = {R(0), R(0), R(0)};
-        R rho0f = R(0), E0f = R(0);
-#pragma unroll
-        for (int v = 0; v < 5; ++v) qf[v] = R(0);
-#pragma unroll
-        for (int c = 0; c < 15; ++c) gf[c] = R(0);
-#pragma unroll
-        for (int s = 0; s < N; ++s) {
-          const int pt = pt_of<N>(d, ln, s);
-          const R w = A.ops.I[f][s];
-#pragma unroll
-          for (int v = 0; v < 5; ++v) qf[v] += w * sq[el * 5 * N3 + v * N3 + pt];
-#pragma unroll
-          for (int c = 0; c < 15; ++c) gf[c] += w * sg[el * 15 * N3 + c * N3 + pt];
-          if (PERT) {
-            rho0f += w * sbg[el * 2 * N3 + pt];
-            E0f += w * sbg[el * 2 * N3 + N3 + pt];
-#pragma unroll
-            for (int n = 0; n < 3; ++n) gr0f[n] += w * sgr0[el * 3 * N3 + n * N3 + pt];
-          }
-        }
-        R s3[3];
-#pragma unroll
-        for (int n = 0; n < 3; ++n) s3[n] = Sl[(n * (N + 1) + f) * N2 + ln];
-        const Pt<R> st = point_state<PERT>(qf, rho0f, E0f, ph);
-        const R p0f = ph.gm1 * E0f;
-        R Ft[5];
-        if (f > 0 && f < N) {
-          R Fi[5], Fv[5];
-          flux_inv(qf, st, s3, Fi);
-          flux_visc<PERT>(st, gf, gr0f, rho0f, p0f, s3, ph, Fv);
-#pragma unroll
-          for (int v = 0; v < 5; ++v) Ft[v] = Fi[v] - Fv[v];
-        } else {
-          const int side = (f == N);
-          const int F = 2 * d + side;
-          const R sgn = side ? R(1) : R(-1);
-          const R mag = sqrt(s3[0] * s3[0] + s3[1] * s3[1] + s3[2] * s3[2]);
-          const R nh[3] = {sgn * s3[0] / mag, sgn * s3[1] / mag, sgn * s3[2] / mag};
-          const int nb = A.m.nbr[e * 6 + F];
-          R Fh[5];
-          if (nb >= 0) {
-            R qR[5];
-#pragma unroll
-            for (int v = 0; v < 5; ++v) qR[v] = sT[(el * 6 + F) * 5 * N2 + v * N2 + ln];
-            R rho0R = R(0), E0R = R(0);
-            if (PERT) {
-              rho0R = sTbg[(el * 6 + F) * 2 * N2 + ln];
-              E0R = sTbg[(el * 6 + F) * 2 * N2 + N2 + ln];
-            }
-            const Pt<R> sR = point_state<PERT>(qR, rho0R, E0R, ph);
-            rusanov<PERT>(qf, st, rho0f, E0f, qR, sR, rho0R, E0R, nh, ph, Fh);
-            R Fv[5];
-            flux_visc<PERT>(st, gf, gr0f, rho0f, p0f, nh, ph, Fv);
-#pragma unroll
-            for (int v = 1; v < 5; ++v)  // neighbour stored F_v . n_out(neighbour) = -F_v . n
-              Fh[v] -= R(0.5) * (Fv[v] - sTv[(el * 6 + F) * 4 * N2 + (v - 1) * N2 + ln]);
-          } else {
-            // walls (Section 5): exact inviscid flux (0, p n, 0); normal traction only;
-            // energy: f.n from the lifted gradient with T = T_top (outer) or the prescribed flux (inner)
-            const R mu = st.rho * ph.nu;
-            const R div = gf[3] + gf[7] + gf[11];
-            R trac = R(0);
-#pragma unroll
-            for (int a = 0; a < 3; ++a)
-#pragma unroll
-              for (int b = 0; b < 3; ++b) {
-                R t = mu * (gf[3 + 3 * a + b] + gf[3 + 3 * b + a]);
-                if (a == b) t -= mu * R(2.0 / 3.0) * div;
-                trac += nh[a] * t * nh[b];
-              }
-            Fh[0] = R(0);
-#pragma unroll
-            for (int a = 0; a < 3; ++a) Fh[1 + a] = (st.p - trac) * nh[a];
-            if (nb == -2) {
-              const R RT = ph.Rgas * ph.T_top;
-              R fn = R(0);
-#pragma unroll
-              for (int b = 0; b < 3; ++b)
-                fn += -ph.CpR * (ph.kappa * (gf[12 + b] / ph.gamma - RT * gf[b]) + ph.kappa_r * (gf[12 + b] - RT * gf[b])) *
-                      nh[b];
-              Fh[4] = fn;
-            } else {
-              Fh[4] = PERT ? R(0) : -ph.bottom_flux;
-            }
-          }
-#pragma unroll
-          for (int v = 0; v < 5; ++v) Ft[v] = sgn * mag * Fh[v];
-        }
-#pragma unroll
-        for (int v = 0; v < 5; ++v)
-#pragma unroll
-          for (int i = 0; i < N; ++i) acc[v][i] += A.ops.D[i][f] * Ft[v];
-      }
-#pragma unroll
-      for (int i = 0; i < N; ++i) {
-        const int pt = pt_of<N>(d, ln, i);
-#pragma unroll
-        for (int v = 0; v < 5; ++v) {
-          if (d == 0) sdiv[el * 5 * N3 + v * N3 + pt] = acc[v][i];
-          else sdiv[el * 5 * N3 + v * N3 + pt] += acc[v][i];
-        }
-      }
-    }
-    __syncthreads();
-  }
-
-  // ---- residual dQ/dt = -div/|J| - M (Eqs. 4, 11), sources of Eqs. 2-3, and the RK combination
   if (active) {
 #pragma unroll
     for (int i = 0; i < N; ++i) {
-      const int pt = N * ln + i;
+      const int pt = line_pt<N, 0>(ln, i);
+      const int si = line_sidx<N, 0, R>(ln, i);
       const size_t gi = (size_t)e * N3 + pt;
       R q[5];
 #pragma unroll
-      for (int v = 0; v < 5; ++v) q[v] = sq[el * 5 * N3 + v * N3 + pt];
-      const R x0 = A.m.x[((size_t)e * 3 + 0) * N3 + pt];
-      const R x1 = A.m.x[((size_t)e * 3 + 1) * N3 + pt];
-      const R x2 = A.m.x[((size_t)e * 3 + 2) * N3 + pt];
+      for (int v = 0; v < 5; ++v) q[v] = sq[v * N3 + pt];
+      const R x0 = __ldg(A.m.x + ((size_t)e * 3 + 0) * N3 + pt);
+      const R x1 = __ldg(A.m.x + ((size_t)e * 3 + 1) * N3 + pt);
+      const R x2 = __ldg(A.m.x + ((size_t)e * 3 + 2) * N3 + pt);
       const R r2 = x0 * x0 + x1 * x1 + x2 * x2;
       const R gr = ph.GM / (r2 * sqrt(r2));  // g = gr * x points outward (the source uses -rho g_vec)
       const R g3[3] = {gr * x0, gr * x1, gr * x2};
@@ -728,18 +690,20 @@ __global__ void __launch_bounds__(EPB * N * N) k_resid(const KArgs<R> A) {
       M[2] = q[0] * g3[1] + ph.twoOmega * q[1];
       M[3] = q[0] * g3[2];
       M[4] = q[1] * g3[0] + q[2] * g3[1] + q[3] * g3[2];
-      const R ij = A.m.invJ[gi];
+      const R ij = __ldg(A.m.invJ + gi);
 #pragma unroll
       for (int v = 0; v < 5; ++v) {
-        R Rv = -sdiv[el * 5 * N3 + v * N3 + pt] * ij - M[v];
-        if (PERT) Rv += (R)A.bg.R0[((size_t)e * 5 + v) * N3 + pt];
+        R Rv = -sdiv[v * N3 + si] * ij - M[v];
+        if (PERT) Rv += (R)__ldg(A.bg.R0 + ((size_t)e * 5 + v) * N3 + pt);
         const size_t oi = ((size_t)e * 5 + v) * N3 + pt;
         if (MODE == kModeResidual) {
           A.out[oi] = Rv;
         } else {
-          const R nv = A.a * A.un[oi] + A.b * (q[v] + A.dt * Rv);
+          const R dR = A.dt * Rv;
+          if (A.out2) A.out2[oi] = A.a2 * A.un2[oi] + A.b2 * q[v] + A.c2 * dR;
+          const R nv = A.a * A.un[oi] + A.b * q[v] + A.c * dR;
           A.out[oi] = nv;
-          sq[el * 5 * N3 + v * N3 + pt] = nv;
+          sq[v * N3 + pt] = nv;
         }
       }
     }
@@ -747,14 +711,15 @@ __global__ void __launch_bounds__(EPB * N * N) k_resid(const KArgs<R> A) {
   if (MODE == kModeRK) {
     __syncthreads();
     if (active && A.T_out) {
-#pragma unroll 1
+#pragma unroll
       for (int d = 0; d < 3; ++d)
 #pragma unroll
         for (int v = 0; v < 5; ++v) {
           R lo = R(0), hi = R(0);
 #pragma unroll
           for (int s = 0; s < N; ++s) {
-            const R val = sq[el * 5 * N3 + v * N3 + pt_of<N>(d, ln, s)];
+            const int pt = d == 0 ? line_pt<N, 0>(ln, s) : (d == 1 ? line_pt<N, 1>(ln, s) : line_pt<N, 2>(ln, s));
+            const R val = sq[v * N3 + pt];
             lo += A.ops.I[0][s] * val;
             hi += A.ops.I[N][s] * val;
           }

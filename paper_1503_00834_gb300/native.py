@@ -25,7 +25,8 @@ STATUS = {0: "ok", 1: "invalid argument", 2: "out of memory", 3: "CUDA error", 4
 # every symbol declared in include/chorus.h
 EXPORTS = ("chorus_mesh_create", "chorus_mesh_destroy", "chorus_mesh_info", "chorus_prepare", "chorus_state_init",
            "chorus_residual", "chorus_rk_workspace_bytes", "chorus_rk_step", "chorus_reduce", "chorus_check",
-           "chorus_strerror", "chorus_timing_enable", "chorus_timing_read", "chorus_residual_noalloc")
+           "chorus_strerror", "chorus_timing_enable", "chorus_timing_read", "chorus_residual_noalloc",
+           "chorus_am_correct", "chorus_rk_step_scheme")
 
 
 class ChorusError(RuntimeError):
@@ -73,6 +74,8 @@ def load() -> ctypes.CDLL:
         "chorus_timing_enable": (i32, [vp, i32]),
         "chorus_timing_read": (i32, [vp, vp, P(f64), P(i64)]),
         "chorus_residual_noalloc": (i32, [vp, P(Params), i32, vp, vp, vp]),
+        "chorus_am_correct": (i32, [vp, P(Params), i32, vp, P(f64), vp]),
+        "chorus_rk_step_scheme": (i32, [vp, P(Params), i32, i32, vp, vp, f64, i64, vp]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(lib, name)
@@ -157,10 +160,23 @@ class Mesh:
         _ok("chorus_rk_step", load().chorus_rk_step(self.handle, ctypes.byref(params), prec, _ptr(Q), _ptr(ws), dt,
                                                     n_steps, _stream(stream)))
 
+    def rk_step_scheme(self, params: Params, prec: int, scheme: int, Q, ws, dt: float, n_steps: int,
+                       stream=None) -> None:
+        """scheme 0: SSP-RK3, 1: SSP-RK(5,4)."""
+        _ok("chorus_rk_step_scheme", load().chorus_rk_step_scheme(self.handle, ctypes.byref(params), prec, scheme,
+                                                                  _ptr(Q), _ptr(ws), dt, n_steps, _stream(stream)))
+
     def reduce(self, params: Params, prec: int, Q, stream=None) -> np.ndarray:
         out = (ctypes.c_double * 4)()
         _ok("chorus_reduce", load().chorus_reduce(self.handle, ctypes.byref(params), prec, _ptr(Q), out,
                                                   _stream(stream)))
+        return np.array(out[:])
+
+    def am_correct(self, params: Params, prec: int, Q, stream=None) -> np.ndarray:
+        """Angular-momentum correction in place; returns delta Omega (synchronises)."""
+        out = (ctypes.c_double * 3)()
+        _ok("chorus_am_correct", load().chorus_am_correct(self.handle, ctypes.byref(params), prec, _ptr(Q), out,
+                                                          _stream(stream)))
         return np.array(out[:])
 
     def timing_enable(self, enable: bool) -> None:

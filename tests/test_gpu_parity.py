@@ -162,6 +162,37 @@ def _noisy_run(osh, Q, dt, n_steps):
     return u
 
 
+@pytest.mark.parametrize("prec", [0, 1], ids=["fp64", "fp32pert"])
+def test_rk54_steps_match_oracle(prec):
+    """The paper's SSP-RK(5,4) (scheme 1) on the 288-element shell against the oracle, on q'."""
+    from oracle import rk
+    from paper_1503_00834_gb300 import FP64
+
+    cfg = SHELL_288_P3
+    n_steps = 10
+    sh = _gpu(cfg)
+    osh = OracleShell(cfg)
+    N = cfg.p + 1
+    Q = _alloc(sh.mesh, prec)[0]
+    sh.mesh.state_init(sh.params, cfg.seed, cfg.entropy_amp, prec, Q)
+    sh.mesh.rk_step_scheme(sh.params, prec, 1, Q, _ws(sh.mesh, prec), sh.dt, n_steps)
+    sh.mesh.check()
+    Qinit = osh.initial_state()
+    Qref = rk.run(osh.disc, osh.ph, Qinit, sh.dt, n_steps, scheme="ssprk54")
+    Q0 = osh.background()
+    W = osh.weights()
+    got = to5(Q, N) - (Q0 if prec == FP64 else 0.0)
+    e, ev = rel_err(got, Qref - Q0, W)
+    print(f"rk54 {n_steps} steps prec {prec}: rel err on q' {ev}")
+    if prec == FP64:
+        from oracle.residual import residual
+
+        kappa = _condition(osh, Qinit, residual(osh.disc, osh.ph, Qinit), W)
+        assert np.all(ev <= 1e-12 * np.maximum(1.0, kappa) + 1e-10)
+    else:
+        assert e < 1e-5
+
+
 def test_reductions_match_oracle():
     from oracle.diagnostics import integrals
     from paper_1503_00834_gb300 import FP32_PERT, FP64

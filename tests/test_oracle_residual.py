@@ -171,6 +171,39 @@ def test_ssprk3_third_order(monkeypatch):
     assert min(rates) > 2.9
 
 
+@pytest.mark.parametrize("lam", [-1.3 + 0.4j, -0.2 + 2.0j])
+def test_ssprk54_fourth_order(monkeypatch, lam):
+    monkeypatch.setattr(rk, "residual", lambda disc, ph, q: lam * q)
+    errs = []
+    for nsteps in (10, 20, 40):
+        y = rk.run(None, None, np.array([1.0 + 0j]), 1.0 / nsteps, nsteps, scheme="ssprk54")
+        errs.append(abs(y[0] - np.exp(lam)))
+    rates = [math.log2(errs[i] / errs[i + 1]) for i in range(2)]
+    assert min(rates) > 3.85, rates
+
+
+def test_ssprk54_fourth_order_nonlinear(monkeypatch):
+    # y' = -y^2 + sin(t)-free autonomous test: y(0) = 1 -> y = 1/(1+t)
+    monkeypatch.setattr(rk, "residual", lambda disc, ph, q: -q * q)
+    errs = []
+    for nsteps in (10, 20, 40):
+        y = rk.run(None, None, np.array([1.0]), 2.0 / nsteps, nsteps, scheme="ssprk54")
+        errs.append(abs(y[0] - 1.0 / 3.0))
+    rates = [math.log2(errs[i] / errs[i + 1]) for i in range(2)]
+    assert min(rates) > 3.85, rates
+
+
+def test_ssprk54_consistency_and_ssp_coefficient():
+    # each stage is a convex combination (coefficients of the u_k sum to one, all non-negative);
+    # the SSP coefficient min(a/b) of the published scheme is about 1.508
+    c = rk.RK54
+    assert abs(c["a20"] + c["a21"] - 1) < 1e-14 and abs(c["a30"] + c["a32"] - 1) < 1e-14
+    assert abs(c["a40"] + c["a43"] - 1) < 1e-14 and abs(c["a52"] + c["a53"] + c["a54"] - 1) < 1e-14
+    ratios = [1.0 / c["b10"], c["a21"] / c["b21"], c["a32"] / c["b32"], c["a43"] / c["b43"], c["a53"] / c["b53"],
+              c["a54"] / c["b54"]]
+    assert abs(min(ratios) - 1.508) < 2e-3
+
+
 def test_initial_state_entropy_perturbation():
     disc = _disc(2, 2, 3)
     _, g = _weights(disc)
