@@ -141,6 +141,65 @@ chorus_status chorus_reduce(chorus_mesh mesh, const chorus_params* params, choru
 chorus_status chorus_am_correct(chorus_mesh mesh, const chorus_params* params, chorus_precision prec,
                                 void* Q, double* domega, void* stream);
 
+/* ---- Learned subgrid closure for coarse (p = 2) runs.
+ * The paper names subgrid-scale modelling as future work (Section 8); the closure is a workload
+ * extension.  Per element, the p = 2 state's departure from the background, q' (27 points x 5
+ * variables, in the state layout, i.e. index v*27 + pt), divided by in_scale[v], feeds a network
+ * 135 -> 128 (SiLU) -> 128 (SiLU) -> 135; its output times out_scale[v] is added to dQ/dt.
+ * Record (device, caller-owned, chorus_closure_bytes() bytes): BF16 W1 [128][135], W2 [128][128],
+ * W3 [135][128] (row-major, output index first), FP32 b1 [128], b2 [128], b3 [135], in_scale [5],
+ * out_scale [5].  Arithmetic accumulates in FP32. */
+size_t chorus_closure_bytes(void);
+
+/* Seeded initial record: weights uniform in +-sqrt(3/fan_in) (output layer x 0.1), zero biases,
+ * the given scales (host float[5] each, > 0).  Synchronises the stream. */
+chorus_status chorus_closure_init(void* weights, uint64_t seed, const float* in_scale, const float* out_scale,
+                                  void* stream);
+
+/* Per-element L2 projection from `fine` to `coarse` (same elements, lower order) in the reference
+ * cube, one direction at a time (P = M_c^-1 B with exact Gauss-Legendre integrals).  kind 0: a
+ * state in the given precision (for FP32_PERT the fine background is added before and the coarse
+ * one subtracted after, both meshes prepared with the same parameters); kind 1: any 5-variable
+ * field such as a residual.  Qf, Qc: device, state layout of each mesh. */
+chorus_status chorus_project(chorus_mesh fine, chorus_mesh coarse, chorus_precision prec, int kind, const void* Qf,
+                             void* Qc, void* stream);
+
+/* Network forward pass on n samples: X, Y device [n][135] FP32. */
+chorus_status chorus_closure_forward(const void* weights, const float* X, float* Y, int64_t n, void* stream);
+
+/* Gradient of L = sum (y - t)^2 / (2 * 135 n) with respect to the parameters (FP32 device vector of
+ * W1, W2, W3, b1, b2, b3 in that order, 51,335 entries, overwritten) and the loss (host).
+ * Synchronises the stream. */
+chorus_status chorus_closure_grad(const void* weights, const float* X, const float* Y, int64_t n, float* grad,
+                                  double* loss, void* stream);
+
+/* Training pairs of one coarse state: X = q'_c / in_scale, Y = (P R_fine - R_coarse) / out_scale per
+ * element (X, Y device [E][135] FP32; Qc, PRf, Rc device in the mesh's state layout and precision). */
+chorus_status chorus_closure_make_pairs(chorus_mesh coarse, chorus_precision prec, const void* weights,
+                                        const void* Qc, const void* PRf, const void* Rc, float* X, float* Y,
+                                        void* stream);
+
+typedef struct {
+  int64_t epochs, batch;        /* passes over the pairs, samples per Adam step */
+  double lr, beta1, beta2, eps; /* Adam (Kingma and Ba) */
+  uint64_t seed;                /* reserved */
+} chorus_train_cfg;
+
+/* Adam training of the record in place on n_pairs pairs (X, Y device [n][135] FP32, taken in order
+ * in batches; shuffle beforehand).  FP32 master weights live in a temporary device workspace; the
+ * record's BF16 weights are rewritten after every step.  losses: host double[epochs] receiving the
+ * mean batch loss of each epoch, or NULL.  Synchronises the stream. */
+chorus_status chorus_closure_train(const float* X, const float* Y, int64_t n_pairs, void* weights,
+                                   const chorus_train_cfg* cfg, double* losses, void* stream);
+
+/* R += closure(Q) for a p = 2 mesh (FP64 needs chorus_prepare for the background). */
+chorus_status chorus_closure_apply(chorus_mesh coarse, chorus_precision prec, const void* weights, const void* Q,
+                                   void* R, void* stream);
+
+/* Attach a record to a p = 2 mesh: chorus_residual and every RK stage then add the closure to
+ * dQ/dt.  NULL detaches.  The record must stay valid while attached. */
+chorus_status chorus_closure_attach(chorus_mesh coarse, const void* weights);
+
 /* Kernel timing for measurement.  While enabled, every kernel that chorus_residual and
  * chorus_rk_step launch is bracketed by a pair of CUDA events recorded on the call's stream (the
  * kernels themselves are unchanged).  chorus_timing_read synchronises the stream and returns, per

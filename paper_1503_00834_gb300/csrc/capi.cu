@@ -8,7 +8,8 @@
 #include <new>
 #include <vector>
 
-#include "../../include/chorus.h"
+#include "chorus.h"
+#include "closure.h"
 #include "internal.h"
 #include "mesh_builder.h"
 #include "sd_tables.h"
@@ -52,6 +53,9 @@ struct chorus_mesh_s {
   bool timing = false;
   std::vector<Rec> recs;
   std::vector<cudaEvent_t> pool;
+  // attached learned closure (p = 2 meshes): record pointer and its per-stage output buffer
+  const void* closure = nullptr;
+  void* closure_buf = nullptr;
 };
 
 namespace {
@@ -360,6 +364,7 @@ cudaError_t timed(chorus_mesh_s* m, int cls, cudaStream_t st, Fn&& fn) {
 }
 
 void free_mesh(chorus_mesh_s* m) {
+  dev_free(m->closure_buf);
   release_records(m);
   for (cudaEvent_t e : m->pool) cudaEventDestroy(e);
   m->pool.clear();
@@ -382,7 +387,8 @@ size_t ws_words(const chorus_mesh_s* m) {
   const size_t N = m->N, E = m->E;
   const size_t N2 = N * N, N3 = N2 * N;
   // stage buffer + two trace buffers + viscous normal-flux traces + two more stage buffers (RK(5,4))
-  return 3 * E * 5 * N3 + 2 * E * 6 * 5 * N2 + E * 6 * 4 * N2;
+  // + the gradient record handed from the gradient kernel to the residual kernel
+  return 3 * E * 5 * N3 + 2 * E * 6 * 5 * N2 + E * 6 * 4 * N2 + E * 12 * N3;
 }
 
 template <class R>
@@ -393,6 +399,7 @@ struct Ws {
   R* Tv;
   R* A;
   R* B;
+  R* G;
 };
 
 template <class R>
@@ -407,6 +414,7 @@ Ws<R> split_ws(const chorus_mesh_s* m, void* w) {
   r.Tv = r.Tb + E * 6 * 5 * N2;
   r.A = r.Tv + E * 6 * 4 * N2;
   r.B = r.A + E * 5 * N3;
+  r.G = r.B + E * 5 * N3;
   return r;
 }
 
@@ -566,9 +574,10 @@ chorus_status chorus_prepare(chorus_mesh m, const chorus_params* P, void* stream
   k_background<<<grid1(nP), 256, 0, st>>>((int64_t)nP, N3, m->d_x64, ph, m->d_Q0);
   ce = cudaGetLastError();
   if (ce == cudaSuccess) ce = m->L.trace64(ma, m->ops64, m->d_Q0, T, st);
-  if (ce == cudaSuccess) ce = m->L.grad64(ma, m->ops64, ph, m->d_Q0, T, Tv, gr, m->d_err, st);
+  if (ce == cudaSuccess) ce = m->L.grad64(ma, m->ops64, ph, m->d_Q0, T, Tv, gr, nullptr, m->d_err, st);
   if (ce == cudaSuccess)
-    ce = m->L.resid64(ma, m->ops64, ph, m->d_Q0, T, Tv, R0, nullptr, RkCoef<double>{}, 0.0, kModeResidual, m->d_err, st);
+    ce = m->L.resid64(ma, m->ops64, ph, m->d_Q0, T, Tv, nullptr, R0, nullptr, RkCoef<double>{}, 0.0, kModeResidual,
+                      m->d_err, st);
   if (ce == cudaSuccess) {
     k_d2f<<<grid1(5 * nP), 256, 0, st>>>((int64_t)(5 * nP), R0, m->d_R0);
     k_d2f<<<grid1(3 * nP), 256, 0, st>>>((int64_t)(3 * nP), gr, m->d_grho0);
@@ -608,9 +617,16 @@ chorus_status chorus_residual(chorus_mesh m, const chorus_params* P, chorus_prec
     const MeshArg<double> ma = mesh_arg<double>(m);
     Ws<double> w = split_ws<double>(m, workspace);
     CHK(timed(m, 0, st, [&] { return m->L.trace64(ma, m->ops64, (const double*)Q, w.Ta, st); }));
-    CHK(timed(m, 1, st, [&] { return m->L.grad64(ma, m->ops64, ph, (const double*)Q, w.Ta, w.Tv, nullptr, m->d_err, st); }));
+    CHK(timed(m, 1, st, [&] {
+      return m->L.grad64(ma, m->ops64, ph, (const double*)Q, w.Ta, w.Tv, nullptr, w.G, m->d_err, st);
+    }));
+    RkCoef<double> rc{};
+    if (m->closure) {
+      CHK(mlp_elements(0, m->closure, Q, m->d_Q0, m->closure_buf, m->E, 0, st));
+      rc.radd = (const double*)m->closure_buf;
+    }
     CHK(timed(m, 2, st, [&] {
-      return m->L.resid64(ma, m->ops64, ph, (const double*)Q, w.Ta, w.Tv, (double*)R, nullptr, RkCoef<double>{}, 0.0,
+      return m->L.resid64(ma, m->ops64, ph, (const double*)Q, w.Ta, w.Tv, w.G, (double*)R, nullptr, rc, 0.0,
                           kModeResidual, m->d_err, st);
     }));
     return CHORUS_OK;
@@ -622,9 +638,14 @@ chorus_status chorus_residual(chorus_mesh m, const chorus_params* P, chorus_prec
   Ws<float> w = split_ws<float>(m, workspace);
   const BgArg bg = bg_arg(m);
   CHK(timed(m, 0, st, [&] { return m->L.trace32(ma, m->ops32, (const float*)Q, w.Ta, st); }));
-  CHK(timed(m, 1, st, [&] { return m->L.grad32(ma, m->ops32, ph, bg, (const float*)Q, w.Ta, w.Tv, m->d_err, st); }));
+  CHK(timed(m, 1, st, [&] { return m->L.grad32(ma, m->ops32, ph, bg, (const float*)Q, w.Ta, w.Tv, w.G, m->d_err, st); }));
+  RkCoef<float> rc{};
+  if (m->closure) {
+    CHK(mlp_elements(1, m->closure, Q, nullptr, m->closure_buf, m->E, 0, st));
+    rc.radd = (const float*)m->closure_buf;
+  }
   CHK(timed(m, 2, st, [&] {
-    return m->L.resid32(ma, m->ops32, ph, bg, (const float*)Q, w.Ta, w.Tv, (float*)R, nullptr, RkCoef<float>{}, 0.0f,
+    return m->L.resid32(ma, m->ops32, ph, bg, (const float*)Q, w.Ta, w.Tv, w.G, (float*)R, nullptr, rc, 0.0f,
                         kModeResidual, m->d_err, st);
   }));
   return CHORUS_OK;
@@ -672,7 +693,12 @@ chorus_status run_rk(chorus_mesh_s* m, R* u, const Ws<R>& w, double dt, int64_t 
   for (int64_t n = 0; n < n_steps; ++n)
     for (const Stage& g : stg) {
       RkCoef<R> c{buf[g.un], (R)g.a, (R)g.b, (R)g.c, g.un2 >= 0 ? buf[g.un2] : nullptr,
-                  g.out2 >= 0 ? buf[g.out2] : nullptr, (R)g.a2, (R)g.b2, (R)g.c2};
+                  g.out2 >= 0 ? buf[g.out2] : nullptr, (R)g.a2, (R)g.b2, (R)g.c2, nullptr};
+      if (m->closure) {
+        CHK(mlp_elements(sizeof(R) == 8 ? 0 : 1, m->closure, buf[g.src], sizeof(R) == 8 ? m->d_Q0 : nullptr,
+                         m->closure_buf, m->E, 0, st));
+        c.radd = (const R*)m->closure_buf;
+      }
       CHK(timed(m, 1, st, [&] { return grad(buf[g.src], Tc); }));
       CHK(timed(m, 2, st, [&] { return resid(buf[g.src], Tc, buf[g.dst], Tn, c); }));
       std::swap(Tc, Tn);
@@ -697,9 +723,11 @@ chorus_status chorus_rk_step_scheme(chorus_mesh m, const chorus_params* P, choru
     Ws<double> w = split_ws<double>(m, workspace);
     return run_rk<double>(
         m, (double*)Q, w, dt, n_steps, scheme, st,
-        [&](const double* q, const double* T) { return m->L.grad64(ma, m->ops64, ph, q, T, w.Tv, nullptr, m->d_err, st); },
+        [&](const double* q, const double* T) {
+          return m->L.grad64(ma, m->ops64, ph, q, T, w.Tv, nullptr, w.G, m->d_err, st);
+        },
         [&](const double* q, const double* T, double* dst, double* Tn, const RkCoef<double>& c) {
-          return m->L.resid64(ma, m->ops64, ph, q, T, w.Tv, dst, Tn, c, dt, kModeRK, m->d_err, st);
+          return m->L.resid64(ma, m->ops64, ph, q, T, w.Tv, w.G, dst, Tn, c, dt, kModeRK, m->d_err, st);
         },
         [&](const double* q, double* T) { return m->L.trace64(ma, m->ops64, q, T, st); });
   }
@@ -711,9 +739,9 @@ chorus_status chorus_rk_step_scheme(chorus_mesh m, const chorus_params* P, choru
   Ws<float> w = split_ws<float>(m, workspace);
   return run_rk<float>(
       m, (float*)Q, w, dt, n_steps, scheme, st,
-      [&](const float* q, const float* T) { return m->L.grad32(ma, m->ops32, ph, bg, q, T, w.Tv, m->d_err, st); },
+      [&](const float* q, const float* T) { return m->L.grad32(ma, m->ops32, ph, bg, q, T, w.Tv, w.G, m->d_err, st); },
       [&](const float* q, const float* T, float* dst, float* Tn, const RkCoef<float>& c) {
-        return m->L.resid32(ma, m->ops32, ph, bg, q, T, w.Tv, dst, Tn, c, (float)dt, kModeRK, m->d_err, st);
+        return m->L.resid32(ma, m->ops32, ph, bg, q, T, w.Tv, w.G, dst, Tn, c, (float)dt, kModeRK, m->d_err, st);
       },
       [&](const float* q, float* T) { return m->L.trace32(ma, m->ops32, q, T, st); });
 }
@@ -777,6 +805,128 @@ chorus_status chorus_am_correct(chorus_mesh m, const chorus_params* P, chorus_pr
     CHK(cudaMemcpyAsync(domega, out + 6, 3 * sizeof(double), cudaMemcpyDeviceToHost, st));
     CHK(cudaStreamSynchronize(st));
   }
+  return CHORUS_OK;
+}
+
+size_t chorus_closure_bytes(void) { return closure_record_bytes(); }
+
+chorus_status chorus_closure_init(void* weights, uint64_t seed, const float* in_scale, const float* out_scale,
+                                  void* stream) {
+  if (!weights || !in_scale || !out_scale) return CHORUS_EINVAL;
+  for (int v = 0; v < 5; ++v)
+    if (!(in_scale[v] > 0.f) || !(out_scale[v] > 0.f)) return CHORUS_EINVAL;
+  const std::vector<unsigned char> rec = init_record(seed, in_scale, out_scale);
+  cudaStream_t st = (cudaStream_t)stream;
+  CHK(cudaMemcpyAsync(weights, rec.data(), rec.size(), cudaMemcpyHostToDevice, st));
+  CHK(cudaStreamSynchronize(st));
+  return CHORUS_OK;
+}
+
+chorus_status chorus_project(chorus_mesh fine, chorus_mesh coarse, chorus_precision prec, int kind, const void* Qf,
+                             void* Qc, void* stream) {
+  if (!fine || !coarse || !Qf || !Qc || fine->E != coarse->E || (kind != 0 && kind != 1) ||
+      (prec != CHORUS_FP64 && prec != CHORUS_FP32_PERT))
+    return CHORUS_EINVAL;
+  const double *add = nullptr, *sub = nullptr;
+  if (kind == 0 && prec == CHORUS_FP32_PERT) {
+    if (!fine->prepared || !coarse->prepared || !same_params(fine->prep, coarse->prep)) return CHORUS_EINVAL;
+    add = fine->d_Q0;
+    sub = coarse->d_Q0;
+  }
+  return cu(launch_project(fine->E, fine->N, coarse->N, prec == CHORUS_FP64 ? 0 : 1, Qf, Qc, add, sub, 5,
+                           (cudaStream_t)stream));
+}
+
+chorus_status chorus_closure_forward(const void* weights, const float* X, float* Y, int64_t n, void* stream) {
+  if (!weights || !X || !Y || n < 0) return CHORUS_EINVAL;
+  if (n == 0) return CHORUS_OK;
+  return cu(mlp_forward(weights, X, Y, n, (cudaStream_t)stream));
+}
+
+chorus_status chorus_closure_grad(const void* weights, const float* X, const float* Y, int64_t n, float* grad,
+                                  double* loss, void* stream) {
+  if (!weights || !X || !Y || !grad || n <= 0) return CHORUS_EINVAL;
+  cudaStream_t st = (cudaStream_t)stream;
+  double* dl = nullptr;
+  CHK(cudaMallocAsync((void**)&dl, sizeof(double), st));
+  CHK(cudaMemsetAsync(dl, 0, sizeof(double), st));
+  CHK(cudaMemsetAsync(grad, 0, ClosureLayout::n_params * sizeof(float), st));
+  cudaError_t e = mlp_backward(weights, X, Y, n, 0, n, grad, dl, st);
+  double h = 0.0;
+  if (e == cudaSuccess) e = cudaMemcpyAsync(&h, dl, sizeof(double), cudaMemcpyDeviceToHost, st);
+  cudaFreeAsync(dl, st);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+  if (loss) *loss = h;
+  return cu(e);
+}
+
+chorus_status chorus_closure_make_pairs(chorus_mesh coarse, chorus_precision prec, const void* weights, const void* Qc,
+                                        const void* PRf, const void* Rc, float* X, float* Y, void* stream) {
+  if (!coarse || coarse->p != 2 || !weights || !Qc || !PRf || !Rc || !X || !Y) return CHORUS_EINVAL;
+  if (prec == CHORUS_FP64 && !coarse->prepared) return CHORUS_EINVAL;
+  return cu(make_pairs(prec == CHORUS_FP64 ? 0 : 1, weights, Qc, prec == CHORUS_FP64 ? coarse->d_Q0 : nullptr, PRf,
+                       Rc, X, Y, coarse->E, (cudaStream_t)stream));
+}
+
+chorus_status chorus_closure_train(const float* X, const float* Y, int64_t n_pairs, void* weights,
+                                   const chorus_train_cfg* cfg, double* losses, void* stream) {
+  if (!X || !Y || !weights || !cfg || n_pairs <= 0 || cfg->epochs <= 0 || cfg->batch <= 0 || !(cfg->lr > 0))
+    return CHORUS_EINVAL;
+  cudaStream_t st = (cudaStream_t)stream;
+  const size_t np = ClosureLayout::n_params;
+  float *master = nullptr, *m1 = nullptr, *m2 = nullptr, *grad = nullptr;
+  double* dl = nullptr;
+  if (dev_alloc(&master, np) || dev_alloc(&m1, np) || dev_alloc(&m2, np) || dev_alloc(&grad, np) ||
+      dev_alloc(&dl, 1)) {
+    dev_free(master); dev_free(m1); dev_free(m2); dev_free(grad); dev_free(dl);
+    return CHORUS_ENOMEM;
+  }
+  cudaError_t e = load_master(weights, master, st);
+  if (e == cudaSuccess) e = cudaMemsetAsync(m1, 0, np * sizeof(float), st);
+  if (e == cudaSuccess) e = cudaMemsetAsync(m2, 0, np * sizeof(float), st);
+  int64_t t = 0;
+  for (int64_t ep = 0; ep < cfg->epochs && e == cudaSuccess; ++ep) {
+    e = cudaMemsetAsync(dl, 0, sizeof(double), st);
+    for (int64_t b0 = 0; b0 < n_pairs && e == cudaSuccess; b0 += cfg->batch) {
+      const int64_t rows = std::min<int64_t>(cfg->batch, n_pairs - b0);
+      e = cudaMemsetAsync(grad, 0, np * sizeof(float), st);
+      if (e == cudaSuccess) e = mlp_backward(weights, X, Y, n_pairs, b0, rows, grad, dl, st);
+      if (e == cudaSuccess)
+        e = adam(master, m1, m2, grad, weights, (float)cfg->lr, (float)cfg->beta1, (float)cfg->beta2, (float)cfg->eps,
+                 ++t, st);
+    }
+    if (losses && e == cudaSuccess) {
+      double h = 0.0;
+      e = cudaMemcpyAsync(&h, dl, sizeof(double), cudaMemcpyDeviceToHost, st);
+      if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+      // each batch added its mean loss; report the mean over batches
+      losses[ep] = h / (double)((n_pairs + cfg->batch - 1) / cfg->batch);
+    }
+  }
+  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+  dev_free(master); dev_free(m1); dev_free(m2); dev_free(grad); dev_free(dl);
+  return cu(e);
+}
+
+chorus_status chorus_closure_apply(chorus_mesh coarse, chorus_precision prec, const void* weights, const void* Q,
+                                   void* R, void* stream) {
+  if (!coarse || coarse->p != 2 || !weights || !Q || !R) return CHORUS_EINVAL;
+  if (prec == CHORUS_FP64 && !coarse->prepared) return CHORUS_EINVAL;
+  return cu(mlp_elements(prec == CHORUS_FP64 ? 0 : 1, weights, Q, prec == CHORUS_FP64 ? coarse->d_Q0 : nullptr, R,
+                         coarse->E, 1, (cudaStream_t)stream));
+}
+
+chorus_status chorus_closure_attach(chorus_mesh coarse, const void* weights) {
+  if (!coarse) return CHORUS_EINVAL;
+  if (weights == nullptr) {
+    coarse->closure = nullptr;
+    return CHORUS_OK;
+  }
+  if (coarse->p != 2) return CHORUS_EINVAL;
+  if (!coarse->closure_buf) {
+    if (dev_alloc((double**)&coarse->closure_buf, (size_t)coarse->E * 5 * 27)) return CHORUS_ENOMEM;
+  }
+  coarse->closure = weights;
   return CHORUS_OK;
 }
 
@@ -870,8 +1020,8 @@ extern "C" chorus_status chorus_residual_noalloc(chorus_mesh m, const chorus_par
     double* T = (double*)scratch;
     double* Tv = T + nT;
     CHK(m->L.trace64(ma, m->ops64, (const double*)Q, T, st));
-    CHK(m->L.grad64(ma, m->ops64, ph, (const double*)Q, T, Tv, nullptr, m->d_err, st));
-    CHK(m->L.resid64(ma, m->ops64, ph, (const double*)Q, T, Tv, (double*)R, nullptr, RkCoef<double>{}, 0.0,
+    CHK(m->L.grad64(ma, m->ops64, ph, (const double*)Q, T, Tv, nullptr, nullptr, m->d_err, st));
+    CHK(m->L.resid64(ma, m->ops64, ph, (const double*)Q, T, Tv, nullptr, (double*)R, nullptr, RkCoef<double>{}, 0.0,
                      kModeResidual, m->d_err, st));
     return CHORUS_OK;
   }
@@ -881,8 +1031,8 @@ extern "C" chorus_status chorus_residual_noalloc(chorus_mesh m, const chorus_par
   float* T = (float*)scratch;
   float* Tv = T + nT;
   CHK(m->L.trace32(ma, m->ops32, (const float*)Q, T, st));
-  CHK(m->L.grad32(ma, m->ops32, ph, bg, (const float*)Q, T, Tv, m->d_err, st));
-  CHK(m->L.resid32(ma, m->ops32, ph, bg, (const float*)Q, T, Tv, (float*)R, nullptr, RkCoef<float>{}, 0.0f,
+  CHK(m->L.grad32(ma, m->ops32, ph, bg, (const float*)Q, T, Tv, nullptr, m->d_err, st));
+  CHK(m->L.resid32(ma, m->ops32, ph, bg, (const float*)Q, T, Tv, nullptr, (float*)R, nullptr, RkCoef<float>{}, 0.0f,
                    kModeResidual, m->d_err, st));
   return CHORUS_OK;
 }

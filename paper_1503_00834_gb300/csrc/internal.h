@@ -52,6 +52,7 @@ enum ResidMode { kModeResidual = 0, kModeRK = 1 };
 // Stage combination of the RK update fused into the residual kernel:
 //   out  = a un  + b q + c dt R
 //   out2 = a2 un2 + b2 q + c2 dt R   (when out2 != nullptr)
+// where R includes `radd` (an additive residual correction, e.g. the learned closure) when non-null.
 template <class R>
 struct RkCoef {
   const R* un;
@@ -59,21 +60,24 @@ struct RkCoef {
   const R* un2;
   R* out2;
   R a2, b2, c2;
+  const R* radd;
 };
 
 // Per-order launchers (defined in kern_p<N>.cu).  All return cudaGetLastError().
 struct LaunchSet {
   cudaError_t (*trace64)(const MeshArg<double>&, const OpsArg<double>&, const double* q, double* T, cudaStream_t);
+  // G: gradient record [E][12][N^3] written by grad (when non-null) and read by resid (when
+  // non-null, resid then skips the lifting)
   cudaError_t (*grad64)(const MeshArg<double>&, const OpsArg<double>&, const PhysArg<double>&, const double* q,
-                        const double* T, double* Tv, double* grad_rho_out, unsigned* err, cudaStream_t);
+                        const double* T, double* Tv, double* grad_rho_out, double* G, unsigned* err, cudaStream_t);
   cudaError_t (*resid64)(const MeshArg<double>&, const OpsArg<double>&, const PhysArg<double>&, const double* q,
-                         const double* T, const double* Tv, double* out, double* T_out, const RkCoef<double>& rk,
-                         double dt, int mode, unsigned* err, cudaStream_t);
+                         const double* T, const double* Tv, const double* G, double* out, double* T_out,
+                         const RkCoef<double>& rk, double dt, int mode, unsigned* err, cudaStream_t);
   cudaError_t (*trace32)(const MeshArg<float>&, const OpsArg<float>&, const float* q, float* T, cudaStream_t);
   cudaError_t (*grad32)(const MeshArg<float>&, const OpsArg<float>&, const PhysArg<float>&, const BgArg&,
-                        const float* q, const float* T, float* Tv, unsigned* err, cudaStream_t);
+                        const float* q, const float* T, float* Tv, float* G, unsigned* err, cudaStream_t);
   cudaError_t (*resid32)(const MeshArg<float>&, const OpsArg<float>&, const PhysArg<float>&, const BgArg&,
-                         const float* q, const float* T, const float* Tv, float* out, float* T_out,
+                         const float* q, const float* T, const float* Tv, const float* G, float* out, float* T_out,
                          const RkCoef<float>& rk, float dt, int mode, unsigned* err, cudaStream_t);
 };
 

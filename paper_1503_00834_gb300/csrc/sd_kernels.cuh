@@ -128,6 +128,8 @@ struct KArgs {
   const R* Tv;         // one-sided normal viscous fluxes [E][6][4][N2] (resid kernel input)
   R* Tv_out;           // grad kernel output
   R* grad_rho_out;     // optional grad kernel output: lifted d rho / d x_n [E][3][N3]
+  R* G_out;            // optional grad kernel output: the gradient record [E][kG][N3] (shared layout)
+  const R* G_in;       // optional resid kernel input: that record (then the lifting is not redone)
   R* out;              // residual or new state
   R* T_out;            // traces of the new state (RK mode)
   const R* un;         // first extra state of the RK combination
@@ -135,6 +137,7 @@ struct KArgs {
   const R* un2;        // optional second output: out2 = a2 un2 + b2 q + c2 dt R
   R* out2;
   R a2, b2, c2;
+  const R* radd;       // optional additive residual correction [E][5][N3]
   unsigned* err;
 };
 
@@ -151,23 +154,68 @@ template <int N, bool PERT, bool WANT_TV, class R>
 __device__ __forceinline__ NbFace<R> load_nb(const KArgs<R>& A, int e, int F, int ln) {
   constexpr int N2 = N * N;
   NbFace<R> f;
-  f.kind = A.m.nbr[e * 6 + F];
+  f.kind = __ldg(A.m.nbr + e * 6 + F);
   if (f.kind >= 0) {
-    const int c = A.m.code[e * 6 + F];
+    const int c = __ldg(A.m.code + e * 6 + F);
     const int tp = map_face_pt<N>(ln, c & 7);
     const size_t base = (size_t)f.kind * 6 + (c >> 3);
 #pragma unroll
-    for (int v = 0; v < 5; ++v) f.q[v] = A.T[(base * 5 + v) * N2 + tp];
+    for (int v = 0; v < 5; ++v) f.q[v] = __ldg(A.T + (base * 5 + v) * N2 + tp);
     if (WANT_TV) {
 #pragma unroll
-      for (int v = 0; v < 4; ++v) f.tv[v] = A.Tv[(base * 4 + v) * N2 + tp];
+      for (int v = 0; v < 4; ++v) f.tv[v] = __ldg(A.Tv + (base * 4 + v) * N2 + tp);
       if (PERT) {
-        f.r0 = (R)A.bg.bgT[(base * 2) * N2 + tp];
-        f.E0 = (R)A.bg.bgT[(base * 2 + 1) * N2 + tp];
+        f.r0 = (R)__ldg(A.bg.bgT + (base * 2) * N2 + tp);
+        f.E0 = (R)__ldg(A.bg.bgT + (base * 2 + 1) * N2 + tp);
       }
     }
   }
   return f;
+}
+
+// Global-memory inputs of one direction sweep, loaded ahead of their use so that their latency
+// overlaps the preceding work (the sweeps otherwise stall on them once per flux point).
+template <int N, class R>
+struct LiftPre {
+  R S[3][N + 1];  // S^D_n at the N+1 flux points of the line
+  R ij[N];        // 1/|J| at the line's solution points
+  NbFace<R> nb[2];
+};
+
+template <class R>
+struct FluxPre {
+  R s3[3];  // S^D_n at flux point 1 of the line (the first one the sweep visits)
+  NbFace<R> nb[2];
+};
+
+template <int N, bool PERT, class R, int D>
+__device__ __forceinline__ void lift_prefetch(const KArgs<R>& A, int e, int ln, LiftPre<N, R>& p) {
+  constexpr int N2 = N * N, N3 = N * N * N;
+  const R* Sl = A.m.Sf + ((size_t)e * 3 + D) * 3 * (N + 1) * N2;
+#pragma unroll
+  for (int n = 0; n < 3; ++n)
+#pragma unroll
+    for (int f = 0; f <= N; ++f) p.S[n][f] = __ldg(Sl + (n * (N + 1) + f) * N2 + ln);
+#pragma unroll
+  for (int i = 0; i < N; ++i) p.ij[i] = __ldg(A.m.invJ + (size_t)e * N3 + line_pt<N, D>(ln, i));
+  p.nb[0] = load_nb<N, PERT, false>(A, e, 2 * D, ln);
+  p.nb[1] = load_nb<N, PERT, false>(A, e, 2 * D + 1, ln);
+}
+
+// Whether the flux sweep's neighbour data are loaded ahead (registers held through the sweep) or at
+// the two end points.
+constexpr bool kFluxNbAhead = true;
+
+template <int N, bool PERT, class R, int D>
+__device__ __forceinline__ void flux_prefetch(const KArgs<R>& A, int e, int ln, FluxPre<R>& p) {
+  constexpr int N2 = N * N;
+  const R* Sl = A.m.Sf + ((size_t)e * 3 + D) * 3 * (N + 1) * N2;
+#pragma unroll
+  for (int n = 0; n < 3; ++n) p.s3[n] = __ldg(Sl + (n * (N + 1) + 1) * N2 + ln);  // flux point 1
+  if (kFluxNbAhead) {
+    p.nb[0] = load_nb<N, PERT, true>(A, e, 2 * D, ln);
+    p.nb[1] = load_nb<N, PERT, true>(A, e, 2 * D + 1, ln);
+  }
 }
 
 // ------------------------------------------------------------------ trace kernel
@@ -200,19 +248,28 @@ __global__ void __launch_bounds__(EPB * N * N) k_trace(const MeshArg<R> m, const
 
 // ------------------------------------------------------------------ staging
 
-template <int N, bool PERT, class R, int EPB>
-__device__ __forceinline__ void stage_elements(const KArgs<R>& A, R* sm, uint64_t* bar, int ne) {
+// `between` runs after the copies are issued and before the wait (it issues the first sweep's
+// global loads so that both latencies overlap).
+template <int N, bool PERT, class R, int EPB, class Between>
+__device__ __forceinline__ void stage_elements(const KArgs<R>& A, R* sm, uint64_t* bar, int ne, Between&& between) {
   using L = Layout<N, PERT, R, EPB>;
   constexpr int N3 = N * N * N;
   const int e0 = blockIdx.x * EPB;
   const bool tq = L::tmaQ && (((uintptr_t)A.q & 15u) == 0);
   const bool tb = PERT && L::tmaBG && (((uintptr_t)A.bg.bg & 15u) == 0) && (((uintptr_t)A.bg.grho0 & 15u) == 0);
-  if (threadIdx.x == 0 && (tq || tb)) {
+  const bool tg = A.G_in != nullptr && ((kG * N3 * sizeof(R)) % 16 == 0) && (((uintptr_t)A.G_in & 15u) == 0);
+  if (A.G_in != nullptr && !tg) {
+    for (int i = threadIdx.x; i < ne * kG * N3; i += blockDim.x)
+      sm[L::oG + (i / (kG * N3)) * L::SG + i % (kG * N3)] = A.G_in[(size_t)e0 * kG * N3 + i];
+  }
+  if (threadIdx.x == 0 && (tq || tb || tg)) {
     uint32_t bytes = 0;
     if (tq) bytes += ne * 5 * N3 * sizeof(R);
     if (tb) bytes += ne * 5 * N3 * sizeof(R);
+    if (tg) bytes += ne * kG * N3 * sizeof(R);
     mbar_expect_tx(bar, bytes);
     for (int el = 0; el < ne; ++el) {
+      if (tg) bulk_g2s(sm + L::oG + el * L::SG, A.G_in + (size_t)(e0 + el) * kG * N3, kG * N3 * sizeof(R), bar);
       if (tq) bulk_g2s(sm + L::oQ + el * L::SQ, A.q + (size_t)(e0 + el) * 5 * N3, 5 * N3 * sizeof(R), bar);
       if (tb) {
         bulk_g2s(sm + L::oBG + el * L::SBG, (const R*)A.bg.bg + (size_t)(e0 + el) * 2 * N3, 2 * N3 * sizeof(R), bar);
@@ -231,7 +288,8 @@ __device__ __forceinline__ void stage_elements(const KArgs<R>& A, R* sm, uint64_
     for (int i = threadIdx.x; i < ne * 3 * N3; i += blockDim.x)
       sm[L::oGR0 + (i / (3 * N3)) * L::SGR0 + i % (3 * N3)] = (R)A.bg.grho0[(size_t)e0 * 3 * N3 + i];
   }
-  if (tq || tb) mbar_wait0(bar, A.err);
+  between();
+  if (tq || tb || tg) mbar_wait0(bar, A.err);
 }
 
 // ------------------------------------------------------------------ lifting, one direction
@@ -239,7 +297,7 @@ __device__ __forceinline__ void stage_elements(const KArgs<R>& A, R* sm, uint64_
 // d q / d xi_D along the thread's D-line with common face values (BR1-like averaging, Section 3;
 // walls Section 5), times grad xi_D = S^D / |J|, accumulated into the gradient array.
 template <int N, bool PERT, class R, int EPB, int D>
-__device__ __forceinline__ void lift_dir(const KArgs<R>& A, R* sm, int el, int ln, int e) {
+__device__ __forceinline__ void lift_dir(const KArgs<R>& A, R* sm, int el, int ln, int e, const LiftPre<N, R>& pre) {
   using L = Layout<N, PERT, R, EPB>;
   constexpr int N2 = N * N, N3 = N * N * N;
   const R* sq = sm + L::oQ + el * L::SQ;
@@ -255,19 +313,13 @@ __device__ __forceinline__ void lift_dir(const KArgs<R>& A, R* sm, int el, int l
     load_line_lin<N, D>(sbg, ln, r0);
     load_line_lin<N, D>(sbg + N3, ln, E0l);
   }
-  R S[3][N + 1];
-  const R* Sl = A.m.Sf + ((size_t)e * 3 + D) * 3 * (N + 1) * N2;
-#pragma unroll
-  for (int n = 0; n < 3; ++n)
-#pragma unroll
-    for (int f = 0; f <= N; ++f) S[n][f] = __ldg(Sl + (n * (N + 1) + f) * N2 + ln);
+  const auto& S = pre.S;
 
   R dq[5][2];  // common state minus own trace at the two ends
 #pragma unroll
   for (int side = 0; side < 2; ++side) {
     const int f = side ? N : 0;
-    const int F = 2 * D + side;
-    const NbFace<R> nb = load_nb<N, PERT, false>(A, e, F, ln);
+    const NbFace<R>& nb = pre.nb[side];
     R qe[5];
 #pragma unroll
     for (int v = 0; v < 5; ++v) {
@@ -307,7 +359,7 @@ __device__ __forceinline__ void lift_dir(const KArgs<R>& A, R* sm, int el, int l
   }
 #pragma unroll
   for (int i = 0; i < N; ++i) {
-    const R ij = __ldg(A.m.invJ + (size_t)e * N3 + line_pt<N, D>(ln, i));
+    const R ij = pre.ij[i];
     R gx[3];
 #pragma unroll
     for (int n = 0; n < 3; ++n) {
@@ -334,15 +386,24 @@ __device__ __forceinline__ void lift_dir(const KArgs<R>& A, R* sm, int el, int l
 
 // Lifting of every element of the CTA; afterwards the first kG component arrays of the gradient
 // array hold the gradient record (grad rho, trace-free strain, grad p) of the form's variables.
+// `pre` holds the direction-0 prefetch on entry; each later direction's loads are issued before
+// the barrier that precedes it.
 template <int N, bool PERT, class R, int EPB>
-__device__ __forceinline__ void lift_all(const KArgs<R>& A, R* sm, int el, int ln, int e, bool active) {
+__device__ __forceinline__ void lift_all(const KArgs<R>& A, R* sm, int el, int ln, int e, bool active,
+                                         LiftPre<N, R>& pre) {
   using L = Layout<N, PERT, R, EPB>;
   constexpr int N3 = N * N * N;
-  if (active) lift_dir<N, PERT, R, EPB, 0>(A, sm, el, ln, e);
+  if (active) {
+    lift_dir<N, PERT, R, EPB, 0>(A, sm, el, ln, e, pre);
+    lift_prefetch<N, PERT, R, 1>(A, e, ln, pre);
+  }
   __syncthreads();
-  if (active) lift_dir<N, PERT, R, EPB, 1>(A, sm, el, ln, e);
+  if (active) {
+    lift_dir<N, PERT, R, EPB, 1>(A, sm, el, ln, e, pre);
+    lift_prefetch<N, PERT, R, 2>(A, e, ln, pre);
+  }
   __syncthreads();
-  if (active) lift_dir<N, PERT, R, EPB, 2>(A, sm, el, ln, e);
+  if (active) lift_dir<N, PERT, R, EPB, 2>(A, sm, el, ln, e, pre);
   __syncthreads();
   if (active) {
     const R* sq = sm + L::oQ + el * L::SQ;
@@ -393,7 +454,8 @@ struct FluxPointData {
 // Lifted gradients, then the one-sided normal viscous flux F_v . n_out on every face point,
 // written for the neighbours: Tv[e][F][0..2] = tau n, Tv[e][F][3] = u.tau n - f.n.
 template <int N, bool PERT, class R, int EPB, int D>
-__device__ __forceinline__ void face_visc_dir(const KArgs<R>& A, const R* sm, int el, int ln, int e) {
+__device__ __forceinline__ void face_visc_dir(const KArgs<R>& A, const R* sm, int el, int ln, int e,
+                                              const R (&s3f)[2][3]) {
   using L = Layout<N, PERT, R, EPB>;
   constexpr int N2 = N * N, N3 = N * N * N;
   const R* sq = sm + L::oQ + el * L::SQ;
@@ -401,7 +463,6 @@ __device__ __forceinline__ void face_visc_dir(const KArgs<R>& A, const R* sm, in
   const R* sgr0 = sm + L::oGR0 + el * L::SGR0;
   const R* sg = sm + L::oG + el * L::SG;
   const R* tI = sm + L::oTAB;
-  const R* Sl = A.m.Sf + ((size_t)e * 3 + D) * 3 * (N + 1) * N2;
   R qv[5][N], gv[kG][N], r0[N], E0l[N], g0[3][N];
 #pragma unroll
   for (int v = 0; v < 5; ++v) load_line_lin<N, D>(sq + v * N3, ln, qv[v]);
@@ -448,7 +509,7 @@ __device__ __forceinline__ void face_visc_dir(const KArgs<R>& A, const R* sm, in
     }
     R s3[3];
 #pragma unroll
-    for (int n = 0; n < 3; ++n) s3[n] = __ldg(Sl + (n * (N + 1) + f) * N2 + ln);
+    for (int n = 0; n < 3; ++n) s3[n] = side ? s3f[1][n] : s3f[0][n];
     const R sgn = side ? R(1) : R(-1);
     const R mag = sqrt(s3[0] * s3[0] + s3[1] * s3[1] + s3[2] * s3[2]);
     const R nh[3] = {sgn * s3[0] / mag, sgn * s3[1] / mag, sgn * s3[2] / mag};
@@ -475,13 +536,33 @@ __global__ void __launch_bounds__(EPB * N * N) k_grad(const KArgs<R> A) {
   if (threadIdx.x == 0) mbar_init(&bar);
   fill_tables<N, R>(A.ops, sm + Layout<N, PERT, R, EPB>::oTAB);
   __syncthreads();
-  stage_elements<N, PERT, R, EPB>(A, sm, &bar, ne);
+  LiftPre<N, R> pre;
+  stage_elements<N, PERT, R, EPB>(A, sm, &bar, ne, [&] {
+    if (active) lift_prefetch<N, PERT, R, 0>(A, e, ln, pre);
+  });
   __syncthreads();
-  lift_all<N, PERT, R, EPB>(A, sm, el, ln, e, active);
+  lift_all<N, PERT, R, EPB>(A, sm, el, ln, e, active, pre);
+  // face metrics of the viscous-flux pass, loaded before the record stores
+  R s3f[3][2][3];
+  if (active && A.Tv_out != nullptr) {
+#pragma unroll
+    for (int d = 0; d < 3; ++d)
+#pragma unroll
+      for (int side = 0; side < 2; ++side)
+#pragma unroll
+        for (int n = 0; n < 3; ++n)
+          s3f[d][side][n] = __ldg(A.m.Sf + ((size_t)e * 3 + d) * 3 * (N + 1) * N2 + (n * (N + 1) + side * N) * N2 + ln);
+  }
+  if (A.G_out != nullptr) {
+    using L = Layout<N, PERT, R, EPB>;
+    constexpr int N3 = N * N * N;
+    for (int i = threadIdx.x; i < ne * kG * N3; i += blockDim.x)
+      A.G_out[(size_t)e0 * kG * N3 + i] = sm[L::oG + (i / (kG * N3)) * L::SG + i % (kG * N3)];
+  }
   if (!active || A.Tv_out == nullptr) return;
-  face_visc_dir<N, PERT, R, EPB, 0>(A, sm, el, ln, e);
-  face_visc_dir<N, PERT, R, EPB, 1>(A, sm, el, ln, e);
-  face_visc_dir<N, PERT, R, EPB, 2>(A, sm, el, ln, e);
+  face_visc_dir<N, PERT, R, EPB, 0>(A, sm, el, ln, e, s3f[0]);
+  face_visc_dir<N, PERT, R, EPB, 1>(A, sm, el, ln, e, s3f[1]);
+  face_visc_dir<N, PERT, R, EPB, 2>(A, sm, el, ln, e, s3f[2]);
 }
 
 // ------------------------------------------------------------------ flux sweep, one direction
@@ -490,7 +571,7 @@ __global__ void __launch_bounds__(EPB * N * N) k_grad(const KArgs<R> A) {
 // the two ends (Rusanov + averaged viscous; walls per Section 5), derivative back to the solution
 // points (Eq. 18), accumulated into the divergence array.
 template <int N, bool PERT, class R, int EPB, int D>
-__device__ __forceinline__ void flux_dir(const KArgs<R>& A, R* sm, int el, int ln, int e) {
+__device__ __forceinline__ void flux_dir(const KArgs<R>& A, R* sm, int el, int ln, int e, const FluxPre<R>& pre) {
   using L = Layout<N, PERT, R, EPB>;
   constexpr int N2 = N * N, N3 = N * N * N;
   const R* sq = sm + L::oQ + el * L::SQ;
@@ -526,8 +607,18 @@ __device__ __forceinline__ void flux_dir(const KArgs<R>& A, R* sm, int el, int l
   const R* tD = sm + L::oTAB + (N + 1) * N;
 
   // one rolled loop over the flux points keeps a single copy of the flux code per direction
+  // Flux points in the order 1, ..., N, 0, so that the neighbour data (prefetched) are first needed
+  // after the interior points; S^D at the next flux point is loaded one iteration ahead.
+  R s3n[3] = {pre.s3[0], pre.s3[1], pre.s3[2]};
 #pragma unroll 1
-  for (int f = 0; f <= N; ++f) {
+  for (int it = 0; it <= N; ++it) {
+    const int f = it < N ? it + 1 : 0;
+    R s3[3] = {s3n[0], s3n[1], s3n[2]};
+    if (it < N) {
+      const int fn = it + 1 < N ? it + 2 : 0;
+#pragma unroll
+      for (int n = 0; n < 3; ++n) s3n[n] = __ldg(Sl + (n * (N + 1) + fn) * N2 + ln);
+    }
     R w[N];
 #pragma unroll
     for (int s = 0; s < N; ++s) w[s] = tI[f * N + s];
@@ -563,9 +654,6 @@ __device__ __forceinline__ void flux_dir(const KArgs<R>& A, R* sm, int el, int l
         for (int n = 0; n < 3; ++n) P.gr0[n] += w[s] * sgr0[n * N3 + pt];
       }
     }
-    R s3[3];
-#pragma unroll
-    for (int n = 0; n < 3; ++n) s3[n] = __ldg(Sl + (n * (N + 1) + f) * N2 + ln);
     const Pt<R> st = point_state<PERT>(P.q, P.r0, P.E0, ph);
     const R p0f = ph.gm1 * P.E0;
     R Ft[5];
@@ -577,8 +665,8 @@ __device__ __forceinline__ void flux_dir(const KArgs<R>& A, R* sm, int el, int l
       for (int v = 0; v < 5; ++v) Ft[v] = Fi[v] - Fv[v];
     } else {
       const int side = (f == N);
-      const int F = 2 * D + side;
-      const NbFace<R> nb = load_nb<N, PERT, true>(A, e, F, ln);
+      const NbFace<R> nb = !kFluxNbAhead ? load_nb<N, PERT, true>(A, e, 2 * D + side, ln)
+                                         : (side ? pre.nb[1] : pre.nb[0]);
       const R sgn = side ? R(1) : R(-1);
       const R mag = sqrt(s3[0] * s3[0] + s3[1] * s3[1] + s3[2] * s3[2]);
       const R nh[3] = {sgn * s3[0] / mag, sgn * s3[1] / mag, sgn * s3[2] / mag};
@@ -655,14 +743,50 @@ __global__ void __launch_bounds__(EPB * N * N, sizeof(R) == 4 ? 3 : 1) k_resid(c
   if (threadIdx.x == 0) mbar_init(&bar);
   fill_tables<N, R>(A.ops, sm + Layout<N, PERT, R, EPB>::oTAB);
   __syncthreads();
-  stage_elements<N, PERT, R, EPB>(A, sm, &bar, ne);
+  const bool lift = A.G_in == nullptr;
+  FluxPre<R> fp;
+  LiftPre<N, R> lp;
+  stage_elements<N, PERT, R, EPB>(A, sm, &bar, ne, [&] {
+    if (!active) return;
+    if (lift) lift_prefetch<N, PERT, R, 0>(A, e, ln, lp);
+    else flux_prefetch<N, PERT, R, 0>(A, e, ln, fp);
+  });
   __syncthreads();
-  lift_all<N, PERT, R, EPB>(A, sm, el, ln, e, active);
-  if (active) flux_dir<N, PERT, R, EPB, 0>(A, sm, el, ln, e);
+  if (lift) {
+    lift_all<N, PERT, R, EPB>(A, sm, el, ln, e, active, lp);
+    if (active) flux_prefetch<N, PERT, R, 0>(A, e, ln, fp);
+  }
+  if (active) {
+    flux_dir<N, PERT, R, EPB, 0>(A, sm, el, ln, e, fp);
+    flux_prefetch<N, PERT, R, 1>(A, e, ln, fp);
+  }
   __syncthreads();
-  if (active) flux_dir<N, PERT, R, EPB, 1>(A, sm, el, ln, e);
+  if (active) {
+    flux_dir<N, PERT, R, EPB, 1>(A, sm, el, ln, e, fp);
+    flux_prefetch<N, PERT, R, 2>(A, e, ln, fp);
+  }
   __syncthreads();
-  if (active) flux_dir<N, PERT, R, EPB, 2>(A, sm, el, ln, e);
+  if (active) flux_dir<N, PERT, R, EPB, 2>(A, sm, el, ln, e, fp);
+
+  // Global inputs of the epilogue, all issued before its first store.  The epilogue works point by
+  // point, so thread ln takes the points ln + N^2 i (i < N): 16 consecutive threads read 64
+  // consecutive bytes of each array.
+  R xg[3][N], ijg[N], r0g[5][N], ung[5][N];
+  if (active) {
+#pragma unroll
+    for (int i = 0; i < N; ++i) {
+      const int pt = ln + N2 * i;
+#pragma unroll
+      for (int n = 0; n < 3; ++n) xg[n][i] = __ldg(A.m.x + ((size_t)e * 3 + n) * N3 + pt);
+      ijg[i] = __ldg(A.m.invJ + (size_t)e * N3 + pt);
+#pragma unroll
+      for (int v = 0; v < 5; ++v) {
+        const size_t oi = ((size_t)e * 5 + v) * N3 + pt;
+        r0g[v][i] = PERT ? (R)__ldg(A.bg.R0 + oi) : R(0);
+        ung[v][i] = (MODE == kModeRK) ? A.un[oi] : R(0);
+      }
+    }
+  }
   __syncthreads();
 
   // residual dQ/dt = -div/|J| - M (Eqs. 4, 11), sources of Eqs. 2-3, and the RK combination
@@ -672,15 +796,12 @@ __global__ void __launch_bounds__(EPB * N * N, sizeof(R) == 4 ? 3 : 1) k_resid(c
   if (active) {
 #pragma unroll
     for (int i = 0; i < N; ++i) {
-      const int pt = line_pt<N, 0>(ln, i);
-      const int si = line_sidx<N, 0, R>(ln, i);
-      const size_t gi = (size_t)e * N3 + pt;
+      const int pt = ln + N2 * i;
+      const int si = sidx<N, R>(ln % N, ln / N, i);
       R q[5];
 #pragma unroll
       for (int v = 0; v < 5; ++v) q[v] = sq[v * N3 + pt];
-      const R x0 = __ldg(A.m.x + ((size_t)e * 3 + 0) * N3 + pt);
-      const R x1 = __ldg(A.m.x + ((size_t)e * 3 + 1) * N3 + pt);
-      const R x2 = __ldg(A.m.x + ((size_t)e * 3 + 2) * N3 + pt);
+      const R x0 = xg[0][i], x1 = xg[1][i], x2 = xg[2][i];
       const R r2 = x0 * x0 + x1 * x1 + x2 * x2;
       const R gr = ph.GM / (r2 * sqrt(r2));  // g = gr * x points outward (the source uses -rho g_vec)
       const R g3[3] = {gr * x0, gr * x1, gr * x2};
@@ -690,18 +811,19 @@ __global__ void __launch_bounds__(EPB * N * N, sizeof(R) == 4 ? 3 : 1) k_resid(c
       M[2] = q[0] * g3[1] + ph.twoOmega * q[1];
       M[3] = q[0] * g3[2];
       M[4] = q[1] * g3[0] + q[2] * g3[1] + q[3] * g3[2];
-      const R ij = __ldg(A.m.invJ + gi);
+      const R ij = ijg[i];
 #pragma unroll
       for (int v = 0; v < 5; ++v) {
         R Rv = -sdiv[v * N3 + si] * ij - M[v];
-        if (PERT) Rv += (R)__ldg(A.bg.R0 + ((size_t)e * 5 + v) * N3 + pt);
+        if (PERT) Rv += r0g[v][i];
         const size_t oi = ((size_t)e * 5 + v) * N3 + pt;
+        if (A.radd) Rv += __ldg(A.radd + oi);
         if (MODE == kModeResidual) {
           A.out[oi] = Rv;
         } else {
           const R dR = A.dt * Rv;
           if (A.out2) A.out2[oi] = A.a2 * A.un2[oi] + A.b2 * q[v] + A.c2 * dR;
-          const R nv = A.a * A.un[oi] + A.b * q[v] + A.c * dR;
+          const R nv = A.a * ung[v][i] + A.b * q[v] + A.c * dR;
           A.out[oi] = nv;
           sq[v * N3 + pt] = nv;
         }

@@ -26,13 +26,23 @@ STATUS = {0: "ok", 1: "invalid argument", 2: "out of memory", 3: "CUDA error", 4
 EXPORTS = ("chorus_mesh_create", "chorus_mesh_destroy", "chorus_mesh_info", "chorus_prepare", "chorus_state_init",
            "chorus_residual", "chorus_rk_workspace_bytes", "chorus_rk_step", "chorus_reduce", "chorus_check",
            "chorus_strerror", "chorus_timing_enable", "chorus_timing_read", "chorus_residual_noalloc",
-           "chorus_am_correct", "chorus_rk_step_scheme")
+           "chorus_am_correct", "chorus_rk_step_scheme", "chorus_closure_bytes", "chorus_closure_init",
+           "chorus_project", "chorus_closure_forward", "chorus_closure_grad", "chorus_closure_make_pairs",
+           "chorus_closure_train", "chorus_closure_apply", "chorus_closure_attach")
 
 
 class ChorusError(RuntimeError):
     def __init__(self, call: str, status: int):
         super().__init__(f"{call}: {STATUS.get(status, status)} (status {status})")
         self.status = status
+
+
+class TrainCfg(ctypes.Structure):
+    """chorus_train_cfg."""
+
+    _fields_ = [("epochs", ctypes.c_int64), ("batch", ctypes.c_int64), ("lr", ctypes.c_double),
+                ("beta1", ctypes.c_double), ("beta2", ctypes.c_double), ("eps", ctypes.c_double),
+                ("seed", ctypes.c_uint64)]
 
 
 class Params(ctypes.Structure):
@@ -76,6 +86,15 @@ def load() -> ctypes.CDLL:
         "chorus_residual_noalloc": (i32, [vp, P(Params), i32, vp, vp, vp]),
         "chorus_am_correct": (i32, [vp, P(Params), i32, vp, P(f64), vp]),
         "chorus_rk_step_scheme": (i32, [vp, P(Params), i32, i32, vp, vp, f64, i64, vp]),
+        "chorus_closure_bytes": (ctypes.c_size_t, []),
+        "chorus_closure_init": (i32, [vp, ctypes.c_uint64, P(ctypes.c_float), P(ctypes.c_float), vp]),
+        "chorus_project": (i32, [vp, vp, i32, i32, vp, vp, vp]),
+        "chorus_closure_forward": (i32, [vp, vp, vp, i64, vp]),
+        "chorus_closure_grad": (i32, [vp, vp, vp, i64, vp, P(f64), vp]),
+        "chorus_closure_make_pairs": (i32, [vp, i32, vp, vp, vp, vp, vp, vp, vp]),
+        "chorus_closure_train": (i32, [vp, vp, i64, vp, P(TrainCfg), P(f64), vp]),
+        "chorus_closure_apply": (i32, [vp, i32, vp, vp, vp, vp]),
+        "chorus_closure_attach": (i32, [vp, vp]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(lib, name)
@@ -191,6 +210,61 @@ class Mesh:
 
     def check(self, stream=None) -> None:
         _ok("chorus_check", load().chorus_check(self.handle, _stream(stream)))
+
+
+# ---------------------------------------------------------------- learned closure
+
+N_PARAMS = 128 * 135 + 128 * 128 + 135 * 128 + 128 + 128 + 135
+
+
+def closure_alloc(seed: int, in_scale, out_scale, stream=None):
+    """A seeded closure record on the device (uint8 tensor)."""
+    import torch
+
+    w = torch.empty(int(load().chorus_closure_bytes()), dtype=torch.uint8, device="cuda")
+    a = (ctypes.c_float * 5)(*in_scale)
+    b = (ctypes.c_float * 5)(*out_scale)
+    _ok("chorus_closure_init", load().chorus_closure_init(_ptr(w), seed, a, b, _stream(stream)))
+    return w
+
+
+def project(fine: "Mesh", coarse: "Mesh", prec: int, kind: int, Qf, Qc, stream=None) -> None:
+    _ok("chorus_project", load().chorus_project(fine.handle, coarse.handle, prec, kind, _ptr(Qf), _ptr(Qc),
+                                                _stream(stream)))
+
+
+def closure_forward(w, X, Y, stream=None) -> None:
+    _ok("chorus_closure_forward", load().chorus_closure_forward(_ptr(w), _ptr(X), _ptr(Y), X.shape[0],
+                                                                _stream(stream)))
+
+
+def closure_grad(w, X, Y, grad, stream=None) -> float:
+    loss = ctypes.c_double()
+    _ok("chorus_closure_grad", load().chorus_closure_grad(_ptr(w), _ptr(X), _ptr(Y), X.shape[0], _ptr(grad),
+                                                          ctypes.byref(loss), _stream(stream)))
+    return loss.value
+
+
+def closure_make_pairs(coarse: "Mesh", prec: int, w, Qc, PRf, Rc, X, Y, stream=None) -> None:
+    _ok("chorus_closure_make_pairs", load().chorus_closure_make_pairs(
+        coarse.handle, prec, _ptr(w), _ptr(Qc), _ptr(PRf), _ptr(Rc), _ptr(X), _ptr(Y), _stream(stream)))
+
+
+def closure_train(X, Y, w, epochs: int, batch: int, lr: float, stream=None):
+    cfg = TrainCfg(epochs, batch, lr, 0.9, 0.999, 1e-8, 0)
+    losses = (ctypes.c_double * epochs)()
+    _ok("chorus_closure_train", load().chorus_closure_train(_ptr(X), _ptr(Y), X.shape[0], _ptr(w), ctypes.byref(cfg),
+                                                            losses, _stream(stream)))
+    return list(losses)
+
+
+def closure_apply(coarse: "Mesh", prec: int, w, Q, R, stream=None) -> None:
+    _ok("chorus_closure_apply", load().chorus_closure_apply(coarse.handle, prec, _ptr(w), _ptr(Q), _ptr(R),
+                                                            _stream(stream)))
+
+
+def closure_attach(coarse: "Mesh", w) -> None:
+    _ok("chorus_closure_attach", load().chorus_closure_attach(coarse.handle, None if w is None else _ptr(w)))
 
 
 def stable_dt(p: int, h_min: float, wave_speed: float, diffusivity: float) -> float:

@@ -1,0 +1,207 @@
+"""GPU learned closure against the oracle.
+
+  * order projection (p = 5 -> p = 2) of states and residuals, and the training pairs built from them;
+  * network forward and parameter gradient against FP64 oracle backpropagation with the same
+    BF16-rounded weights (FP32 accumulation on the GPU: 1e-5 relative forward, 1e-4 gradient);
+  * training on pairs from a seeded p = 5 run reduces the loss, and the trained closure reduces the
+    error of the p = 2 residual against the projected p = 5 residual on held-out snapshots;
+  * an attached closure enters chorus_residual exactly as chorus_closure_apply.
+"""
+import numpy as np
+import pytest
+
+from chorus_inputs import small_shell
+from gpu_common import OracleShell, rel_err, to5
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+
+IN_SCALE = [1e-3, 1e-3, 1e-3, 1e-3, 1e-3]
+OUT_SCALE = [1e-2, 1e-2, 1e-2, 1e-2, 1e-2]
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _built():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1503_00834_gb300 import build
+
+    build.build()
+
+
+def _bf16_to_f64(raw: np.ndarray) -> np.ndarray:
+    return (raw.astype(np.uint32) << 16).view(np.float32).astype(np.float64)
+
+
+def _oracle_params(w):
+    """Decode a closure record (device uint8 tensor) into FP64 oracle parameters."""
+    b = w.cpu().numpy()
+    NI, NH, NO = 135, 128, 135
+    o = 0
+    W = []
+    for n_o, n_i in ((NH, NI), (NH, NH), (NO, NH)):
+        raw = b[o:o + 2 * n_o * n_i].view(np.uint16)
+        W.append(_bf16_to_f64(raw).reshape(n_o, n_i))
+        o += 2 * n_o * n_i
+    bs = []
+    for n in (NH, NH, NO):
+        bs.append(b[o:o + 4 * n].view(np.float32).astype(np.float64))
+        o += 4 * n
+    return dict(W1=W[0], W2=W[1], W3=W[2], b1=bs[0], b2=bs[1], b3=bs[2])
+
+
+def _pair(n=2, n_r=2):
+    from paper_1503_00834_gb300 import Shell
+
+    return Shell(small_shell(n, n_r, 5)), Shell(small_shell(n, n_r, 2))
+
+
+def test_projection_and_pairs_match_oracle():
+    from oracle.closure import project, projection_matrix
+    from oracle.residual import residual
+    from paper_1503_00834_gb300 import FP32_PERT, FP64, native
+
+    fine, coarse = _pair()
+    of, oc = OracleShell(fine.cfg), OracleShell(coarse.cfg)
+    P = projection_matrix(6, 3)
+    Qf = of.initial_state()
+    ref = project(Qf, P)
+    # FP64: the compared perturbation (amplitude 1e-3) is the difference of projected O(1) totals, each
+    # a sum of 6^3 products, so rounding is bounded by about 6^3 x 1e3 x 1.1e-16 = 2.4e-11 relative.
+    for prec, tol in ((FP64, 2.4e-11), (FP32_PERT, 1e-6)):
+        dt = torch.float64 if prec == FP64 else torch.float32
+        qf = torch.empty(fine.mesh.state_shape(), dtype=dt, device="cuda")
+        fine.mesh.state_init(fine.params, fine.cfg.seed, fine.cfg.entropy_amp, prec, qf)
+        coarse.mesh.prepare(coarse.params)
+        qc = torch.empty(coarse.mesh.state_shape(), dtype=dt, device="cuda")
+        native.project(fine.mesh, coarse.mesh, prec, 0, qf, qc)
+        torch.cuda.synchronize()
+        got = to5(qc, 3) + (oc.background() if prec == FP32_PERT else 0.0)
+        e, _ = rel_err(got - oc.background(), ref - oc.background(), oc.weights())
+        assert e < tol, (prec, e)
+    # training pairs of the projected initial state (FP64 path)
+    w = native.closure_alloc(1, IN_SCALE, OUT_SCALE)
+    qf = torch.empty(fine.mesh.state_shape(), dtype=torch.float64, device="cuda")
+    fine.mesh.state_init(fine.params, fine.cfg.seed, fine.cfg.entropy_amp, FP64, qf)
+    wsf = torch.empty(fine.mesh.workspace_bytes(FP64), dtype=torch.uint8, device="cuda")
+    wsc = torch.empty(coarse.mesh.workspace_bytes(FP64), dtype=torch.uint8, device="cuda")
+    Rf = torch.empty_like(qf)
+    fine.mesh.residual(fine.params, FP64, qf, Rf, wsf)
+    qc = torch.empty(coarse.mesh.state_shape(), dtype=torch.float64, device="cuda")
+    PRf = torch.empty_like(qc)
+    Rc = torch.empty_like(qc)
+    native.project(fine.mesh, coarse.mesh, FP64, 0, qf, qc)
+    native.project(fine.mesh, coarse.mesh, FP64, 1, Rf, PRf)
+    coarse.mesh.residual(coarse.params, FP64, qc, Rc, wsc)
+    X = torch.empty((coarse.cfg.n_elem, 135), dtype=torch.float32, device="cuda")
+    Y = torch.empty_like(X)
+    native.closure_make_pairs(coarse.mesh, FP64, w, qc, PRf, Rc, X, Y)
+    torch.cuda.synchronize()
+    Qc_ref = project(Qf, P)
+    PR_ref = project(residual(of.disc, of.ph, Qf), P)
+    Rc_ref = residual(oc.disc, oc.ph, Qc_ref)
+    Xr = ((Qc_ref - oc.background()) / 1e-3).reshape(-1, 135)
+    Yr = ((PR_ref - Rc_ref) / 1e-2).reshape(-1, 135)
+    assert np.allclose(X.cpu().numpy(), Xr, rtol=1e-5, atol=1e-5 * np.abs(Xr).max())
+    assert np.allclose(Y.cpu().numpy(), Yr, rtol=1e-4, atol=1e-5 * np.abs(Yr).max())
+
+
+def test_network_forward_and_gradient_match_oracle():
+    from oracle.closure import forward, loss_and_grad
+    from paper_1503_00834_gb300 import native
+
+    w = native.closure_alloc(7, IN_SCALE, OUT_SCALE)
+    p = _oracle_params(w)
+    rng = np.random.default_rng(0)
+    n = 300  # several tiles and a ragged tail
+    X = rng.standard_normal((n, 135)).astype(np.float32)
+    T = (0.3 * rng.standard_normal((n, 135))).astype(np.float32)
+    Xd, Td = torch.tensor(X, device="cuda"), torch.tensor(T, device="cuda")
+    Yd = torch.empty_like(Xd)
+    native.closure_forward(w, Xd, Yd)
+    Yref, _ = forward(p, X.astype(np.float64))
+    assert np.allclose(Yd.cpu().numpy(), Yref, rtol=1e-5, atol=1e-5 * np.abs(Yref).max())
+    g = torch.empty(native.N_PARAMS, dtype=torch.float32, device="cuda")
+    loss = native.closure_grad(w, Xd, Td, g)
+    lref, gref = loss_and_grad(p, X.astype(np.float64), T.astype(np.float64))
+    assert abs(loss - lref) < 1e-5 * lref
+    flat = np.concatenate([gref[k].reshape(-1) for k in ("W1", "W2", "W3", "b1", "b2", "b3")])
+    got = g.cpu().numpy().astype(np.float64)
+    assert np.linalg.norm(got - flat) < 1e-4 * np.linalg.norm(flat)
+
+
+def _collect(fine, coarse, w, n_snap, every, prec):
+    from paper_1503_00834_gb300 import native
+
+    dt_ = torch.float32
+    qf = torch.empty(fine.mesh.state_shape(), dtype=dt_, device="cuda")
+    fine.mesh.state_init(fine.params, fine.cfg.seed, 1e-2, prec, qf)
+    coarse.mesh.prepare(coarse.params)
+    wsf = torch.empty(fine.mesh.workspace_bytes(prec), dtype=torch.uint8, device="cuda")
+    wsc = torch.empty(coarse.mesh.workspace_bytes(prec), dtype=torch.uint8, device="cuda")
+    Xs, Ys = [], []
+    for _ in range(n_snap):
+        fine.mesh.rk_step(fine.params, prec, qf, wsf, fine.dt, every)
+        Rf = torch.empty_like(qf)
+        fine.mesh.residual(fine.params, prec, qf, Rf, wsf)
+        qc = torch.empty(coarse.mesh.state_shape(), dtype=dt_, device="cuda")
+        PRf, Rc = torch.empty_like(qc), torch.empty_like(qc)
+        native.project(fine.mesh, coarse.mesh, prec, 0, qf, qc)
+        native.project(fine.mesh, coarse.mesh, prec, 1, Rf, PRf)
+        coarse.mesh.residual(coarse.params, prec, qc, Rc, wsc)
+        X = torch.empty((coarse.cfg.n_elem, 135), dtype=torch.float32, device="cuda")
+        Y = torch.empty_like(X)
+        native.closure_make_pairs(coarse.mesh, prec, w, qc, PRf, Rc, X, Y)
+        Xs.append(X)
+        Ys.append(Y)
+    return Xs, Ys
+
+
+def test_training_reduces_loss_and_held_out_error():
+    from paper_1503_00834_gb300 import FP32_PERT, native
+
+    fine, coarse = _pair(4, 3)
+    w = native.closure_alloc(3, IN_SCALE, OUT_SCALE)
+    Xs, Ys = _collect(fine, coarse, w, n_snap=16, every=4, prec=FP32_PERT)
+    g = torch.Generator(device="cpu").manual_seed(0)
+    Xtr, Ytr = torch.cat(Xs[:12]), torch.cat(Ys[:12])
+    perm = torch.randperm(Xtr.shape[0], generator=g).to("cuda")
+    Xtr, Ytr = Xtr[perm].contiguous(), Ytr[perm].contiguous()
+    Xte, Yte = torch.cat(Xs[12:]), torch.cat(Ys[12:])
+    losses = native.closure_train(Xtr, Ytr, w, epochs=150, batch=256, lr=1e-3)
+    print(f"training loss {losses[0]:.4g} -> {losses[-1]:.4g}")
+    assert losses[-1] < 0.5 * losses[0]
+    Yp = torch.empty_like(Xte)
+    native.closure_forward(w, Xte, Yp)
+    err_with = torch.linalg.norm(Yp - Yte).item()
+    err_without = torch.linalg.norm(Yte).item()
+    print(f"held-out |P R5 - R2 - C| / |P R5 - R2| = {err_with / err_without:.4f}")
+    assert err_with < 0.95 * err_without
+
+
+def test_attached_closure_enters_the_residual():
+    from oracle.closure import forward
+    from paper_1503_00834_gb300 import FP32_PERT, native
+
+    _, coarse = _pair()
+    w = native.closure_alloc(5, IN_SCALE, OUT_SCALE)
+    q = torch.empty(coarse.mesh.state_shape(), dtype=torch.float32, device="cuda")
+    coarse.mesh.state_init(coarse.params, coarse.cfg.seed, 1e-2, FP32_PERT, q)
+    ws = torch.empty(coarse.mesh.workspace_bytes(FP32_PERT), dtype=torch.uint8, device="cuda")
+    R0 = torch.empty_like(q)
+    coarse.mesh.residual(coarse.params, FP32_PERT, q, R0, ws)
+    native.closure_attach(coarse.mesh, w)
+    R1 = torch.empty_like(q)
+    coarse.mesh.residual(coarse.params, FP32_PERT, q, R1, ws)
+    native.closure_attach(coarse.mesh, None)
+    R2 = R0.clone()
+    native.closure_apply(coarse.mesh, FP32_PERT, w, q, R2)
+    torch.cuda.synchronize()
+    assert torch.allclose(R1, R2, rtol=1e-6, atol=1e-6 * R1.abs().max().item())
+    # the correction itself against the oracle network
+    C = (R1 - R0).double().cpu().numpy().reshape(-1, 135)
+    X = (q.double().cpu().numpy().reshape(-1, 135) / 1e-3)
+    Yref, _ = forward(_oracle_params(w), X)
+    # C is a difference of two FP32 residuals, so compare to FP32 rounding of the residual size
+    assert np.allclose(C, Yref * 1e-2, rtol=1e-3, atol=1e-3 * np.abs(Yref * 1e-2).max())
