@@ -204,7 +204,7 @@ __device__ __forceinline__ void lift_prefetch(const KArgs<R>& A, int e, int ln, 
 
 // Whether the flux sweep's neighbour data are loaded ahead (registers held through the sweep) or at
 // the two end points.
-constexpr bool kFluxNbAhead = true;
+constexpr bool kFluxNbAhead = false;
 
 template <int N, bool PERT, class R, int D>
 __device__ __forceinline__ void flux_prefetch(const KArgs<R>& A, int e, int ln, FluxPre<R>& p) {
