@@ -7,6 +7,11 @@ time step = 3 passes of the whole residual + stage update; the metric counts sol
 updates per stage (DOF = elements x N^3, Eq. 19).
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl chorus|reference] [--prec fp32|fp64]
+                  [--workload batch_64]
+
+--workload batch_64 times the batch of 64 independent shells (orders 2-5, uneven sizes, 176M
+solution points) advanced together: per-order union meshes, forked streams, a captured step graph,
+tile shapes from the autotuner.
 
 --impl reference times the plain FP64 CPU oracle (the only reference implementation: the paper
 ships no code) on the host cores, on a bounded sample of the same workload.
@@ -143,6 +148,112 @@ def run_reference(args, cfg):
     return value, times, n_sample
 
 
+def run_batch(args, rank, world, local):
+    """Batched independent shells: K graph-replayed SSP-RK3 steps of the whole batch."""
+    import torch
+
+    from chorus_inputs import BATCH_64
+
+    torch.cuda.set_device(local)
+    if world > 1:
+        import torch.distributed as dist
+
+        dist.init_process_group("nccl")
+    from paper_1503_00834_gb300 import Shells, build as _build
+
+    _build.build()
+    stream = torch.cuda.current_stream()
+    t0 = time.perf_counter()
+    sh = Shells(BATCH_64)
+    b = sh.batch
+    build_s = time.perf_counter() - t0
+    Q = torch.empty(b.n_state, dtype=torch.float32, device="cuda")
+    ws = torch.empty(b.workspace_bytes, dtype=torch.uint8, device="cuda")
+    choice = b.autotune(Q, ws, sh.dt, n_trials=2)
+    b.init(Q)
+    launches = b.rk_step(Q, ws, sh.dt, max(3, args.warmup))
+    torch.cuda.synchronize()
+    if world > 1:
+        torch.distributed.barrier()
+    torch.cuda.synchronize()
+    clk = ClockSampler(local)
+    clk.start()
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    ev0.record(stream)
+    b.rk_step(Q, ws, sh.dt, args.steps)
+    ev1.record(stream)
+    torch.cuda.synchronize()
+    if world > 1:
+        torch.distributed.barrier()
+    torch.cuda.synchronize()
+    clocks = clk.stop()
+    ms = ev0.elapsed_time(ev1)
+    if world > 1:
+        t = torch.tensor([ms], device="cuda")
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        ms = float(t.item())
+    red = b.reduce(Q)  # also reports any device-side error flag
+    n_dof = b.n_dof()
+    stages = 3 * args.steps
+    value = world * n_dof * stages / (ms / 1e3)
+    alg = sum(e * (p + 1) ** 3 * ALG_BYTES_PER_DOF_STAGE[p] for e, p in zip(b.n_elem, b.orders))
+    peak, peak_kind = _peaks()
+    achieved = alg / (ms / stages / 1e3) / 1e9
+    # end to end: H2D of the whole batch state, one step, D2H of the state
+    host = torch.empty(Q.shape, dtype=Q.dtype, pin_memory=True)
+    host.copy_(Q)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    e0.record(stream)
+    for _ in range(args.e2e_steps):
+        Q.copy_(host, non_blocking=True)
+        b.rk_step(Q, ws, sh.dt, 1)
+        host.copy_(Q, non_blocking=True)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    e2e_value = world * n_dof * 3 * args.e2e_steps / (e0.elapsed_time(e1) / 1e3)
+    state_bytes = Q.numel() * Q.element_size()
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        class _A:
+            pass
+
+        a = _A()
+        a.ref_elems, a.warmup, a.steps = args.ref_elems, 1, 1
+        cfg0 = next(c for c in sh.cfgs if c.p == 3)
+        v, times, n_sample = run_reference(a, cfg0)
+        a.steps = max(1, int(args.cpu_seconds / max(times[0], 1e-3)))
+        v, times, n_sample = run_reference(a, cfg0)
+        cpu = {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle",
+               "sample": f"{len(times)} x (residual + stage update) on elements 0..{n_sample - 1} of batch shell "
+                         f"{cfg0.name} (p=3; numpy FP64, single thread), {sum(times):.1f} s"}
+    if rank == 0:
+        from collections import Counter
+
+        print(json.dumps({
+            "metric": "RK-stage DOF updates/s, batch of independent shells", "value": value, "unit": UNIT,
+            "n_gpus": world, "steps": args.steps, "warmup": max(3, args.warmup), "ms_per_step": ms / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": BATCH_64.name, "shells": len(sh.cfgs), "elements": sum(b.n_elem), "dof": n_dof,
+                       "orders": dict(Counter(b.orders)), "precision": "FP32 perturbation + FP64 background",
+                       "step": "one SSP-RK3 step of every shell (captured graph, one launch per kernel and order)",
+                       "tiles_elements_per_cta_p2_to_p5": choice, "dt": sh.dt,
+                       "l2": "inputs larger than L2 (state %.0f MB)" % (state_bytes / 1e6),
+                       "build_s": build_s, "parallelism": f"replicas x{world}"},
+            "roofline": {"bound": "hbm", "kernel": "whole step (all kernels of all orders)", "achieved": achieved,
+                         "peak": peak, "unit": "GB/s", "frac": achieved / peak, "traffic": None,
+                         "peak_kind": peak_kind},
+            "gpu_launches": int(launches * args.steps),
+            "clocks": clocks,
+            "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": state_bytes,
+                    "d2h_bytes_per_step": state_bytes},
+            "cpu_baseline": cpu,
+            "mass_total": float(red[:, 0].sum()),
+        }))
+    if world > 1:
+        torch.distributed.destroy_process_group()
+
+
 def main():
     from chorus_inputs import CONFIGS
 
@@ -158,14 +269,22 @@ def main():
     ap.add_argument("--ref-elems", type=int, default=256)
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--workload", default=None, choices=["batch_64"])
     args = ap.parse_args()
     cfg = CONFIGS[args.config]
     rank, world, local = _dist()
     N = cfg.p + 1
+    if args.workload == "batch_64" and args.impl == "chorus":
+        run_batch(args, rank, world, local)
+        return
 
     if args.impl == "reference":
         if rank != 0:
             return
+        if args.workload == "batch_64":
+            from chorus_inputs import BATCH_64
+
+            cfg = next(c for c in BATCH_64.shells() if c.p == 3)
         value, times, n_sample = run_reference(args, cfg)
         line = {
             "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,

@@ -190,7 +190,14 @@ SHELL_786432_P4 = ShellConfig("shell_786432_p4", 64, 32, 4, 0.71, 1.0, 3, 1e-3, 
 SHELL_98304_P3 = ShellConfig("shell_98304_p3", 32, 16, 3, 0.75, 1.0, 2, 1e-3, 100,
                              make_phys(0.75, 1.5, 3.0, 1e-3))
 
-CONFIGS = {c.name: c for c in (SHELL_288_P3, SHELL_331776_P3, SHELL_786432_P4, SHELL_98304_P3)}
+# learned-closure workload: the 98,304-element shell at p = 2 (coarse) and p = 5 (fine, pair source)
+SHELL_98304_P2 = ShellConfig("shell_98304_p2", 32, 16, 2, 0.75, 1.0, 5, 1e-3, 2000,
+                             make_phys(0.75, 1.5, 3.0, 1e-3))
+SHELL_98304_P5 = ShellConfig("shell_98304_p5", 32, 16, 5, 0.75, 1.0, 5, 1e-3, 2000,
+                             make_phys(0.75, 1.5, 3.0, 1e-3))
+
+CONFIGS = {c.name: c for c in (SHELL_288_P3, SHELL_331776_P3, SHELL_786432_P4, SHELL_98304_P3, SHELL_98304_P2,
+                               SHELL_98304_P5)}
 
 
 def small_shell(n: int, n_r: int, p: int, seed: int = 7, amp: float = 1e-3, beta: float = 0.75,
@@ -198,3 +205,59 @@ def small_shell(n: int, n_r: int, p: int, seed: int = 7, amp: float = 1e-3, beta
     """A small shell of the same family for tests."""
     return ShellConfig(f"shell_{n}x{n_r}_p{p}", n, n_r, p, beta, 1.0, seed, amp, 10,
                        make_phys(beta, 1.5, N_rho, 1e-3))
+
+
+def _splitmix64_next(state: int):
+    """One step of SplitMix64 (Steele, Lea and Flood 2014): returns (new state, output)."""
+    m = (1 << 64) - 1
+    state = (state + 0x9E3779B97F4A7C15) & m
+    z = state
+    z = ((z ^ (z >> 30)) * 0xBF58476D1CE4E5B9) & m
+    z = ((z ^ (z >> 27)) * 0x94D049BB133111EB) & m
+    return state, z ^ (z >> 31)
+
+
+@dataclasses.dataclass(frozen=True)
+class BatchConfig:
+    """Independent shells advanced together: shell i draws its lateral cells per panel edge
+    n in [n_lo, n_hi], radial layers n_r in [nr_lo, nr_hi] and order p in `orders` from a SplitMix64
+    stream seeded with seed * 1000 + i, which is also its perturbation seed.  All shells share the
+    radii and the physics of `phys`."""
+
+    name: str
+    n_shells: int
+    seed: int
+    n_lo: int
+    n_hi: int
+    nr_lo: int
+    nr_hi: int
+    orders: tuple
+    r_inner: float
+    r_outer: float
+    entropy_amp: float
+    phys: PhysParams
+
+    def shells(self):
+        out = []
+        for i in range(self.n_shells):
+            s = self.seed * 1000 + i
+            st, a = _splitmix64_next(s)
+            st, b = _splitmix64_next(st)
+            st, c = _splitmix64_next(st)
+            n = self.n_lo + a % (self.n_hi - self.n_lo + 1)
+            n_r = self.nr_lo + b % (self.nr_hi - self.nr_lo + 1)
+            p = self.orders[c % len(self.orders)]
+            out.append(ShellConfig(f"{self.name}_{i}", n, n_r, p, self.r_inner, self.r_outer, s, self.entropy_amp,
+                                   10, self.phys))
+        return out
+
+
+# 64 shells of the shell_288_p3 family (beta 0.75, 3 density scale heights), n 8-32, n_r 4-16, p 2-5
+BATCH_64 = BatchConfig("batch_64", 64, 4, 8, 32, 4, 16, (2, 3, 4, 5), 0.75, 1.0, 1e-3,
+                       make_phys(0.75, 1.5, 3.0, 1e-3))
+
+
+def small_batch() -> BatchConfig:
+    """A small batch of the same family for tests (every order, ragged sizes)."""
+    return BatchConfig("batch_small", 6, 9, 1, 3, 1, 3, (2, 3, 4, 5), 0.75, 1.0, 1e-3,
+                       make_phys(0.75, 1.5, 3.0, 1e-3))

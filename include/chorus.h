@@ -228,6 +228,66 @@ chorus_status chorus_timing_read(chorus_mesh mesh, void* stream, double* ms, int
 chorus_status chorus_residual_noalloc(chorus_mesh mesh, const chorus_params* params, chorus_precision prec,
                                       const void* Q, void* R, void* stream);
 
+/* ---- Batched independent shells -------------------------------------------------------------
+ * Many independent shell instances of different resolution and order advanced together, for
+ * ensembles and parameter studies (the paper runs one shell at a time; this is a throughput mode
+ * of the same discretisation, Sections 3-5).  All shells share the radii and the physical
+ * parameters; each has its own mesh, order and seeded perturbation.
+ *  - Shells of one order form one internal mesh (their disjoint union), so each kernel of an RK
+ *    stage is one launch per order present, and the orders run concurrently on forked streams.
+ *    One RK step of the whole batch is captured once as a CUDA graph and replayed.
+ *  - State: FP32 perturbation form (CHORUS_FP32_PERT) only.  One caller-owned device array holds
+ *    every shell; shell s occupies [state_offset[s], state_offset[s] + n_elem_s * 5 * N_s^3)
+ *    floats, in the single-mesh layout of its own order.
+ *  - A shell of the batch computes bit for bit what a single mesh of that shell computes with the
+ *    same tile shape (the union adds no coupling: shells share no faces). */
+typedef struct chorus_batch_s* chorus_batch;
+
+typedef struct {
+  int64_t n_nodes;
+  const double* node_xyz; /* host [n_nodes][3] */
+  int64_t n_elem;
+  const int64_t* hex20;   /* host [n_elem][20], 0-based, order as in chorus_mesh_create */
+  int p;                  /* 2..5 */
+  uint64_t seed;          /* perturbation seed (as chorus_state_init) */
+  double entropy_amp;     /* perturbation amplitude (as chorus_state_init), 0 <= amp < 1 */
+} chorus_shell_desc;
+
+/* Build the batch: one mesh per order present (curl-form metrics), its background for params
+ * (as chorus_prepare) and the forked streams.  Synchronises. */
+chorus_status chorus_batch_create(int n_shells, const chorus_shell_desc* shells, double r_inner, double r_outer,
+                                  const chorus_params* params, void* stream, chorus_batch* out);
+chorus_status chorus_batch_destroy(chorus_batch batch);
+
+/* state_offset: host int64[n_shells] (float offsets, see above) or NULL; n_state: total floats;
+ * workspace_bytes: bytes of the workspace chorus_batch_rk_step needs; n_groups: orders present;
+ * group_p, group_h_min: host arrays of 4 receiving, per order present (ascending), the order and
+ * the shortest element edge chord of its shells (for the caller's time-step choice), or NULL.
+ * Any output may be NULL. */
+chorus_status chorus_batch_layout(chorus_batch batch, int64_t* state_offset, int64_t* n_state,
+                                  size_t* workspace_bytes, int* n_groups, int* group_p, double* group_h_min);
+
+/* Seeded perturbation of every shell (shell s as chorus_state_init of its own mesh with its seed). */
+chorus_status chorus_batch_init(chorus_batch batch, float* Q, void* stream);
+
+/* n_steps SSP-RK3 steps of size dt for every shell.  The step graph is captured on the first call
+ * for (Q, workspace, dt) and replayed; a call with other pointers or dt captures again.
+ * launches: host int64 receiving the kernel launches per step, or NULL. */
+chorus_status chorus_batch_rk_step(chorus_batch batch, float* Q, void* workspace, double dt, int64_t n_steps,
+                                   void* stream, int64_t* launches);
+
+/* Per-shell FP64 reductions of the total state as chorus_reduce: out host double[n_shells][4]
+ * (mass, total energy, kinetic energy, |L|).  Synchronises. */
+chorus_status chorus_batch_reduce(chorus_batch batch, const float* Q, double* out, void* stream);
+
+/* Tile-shape autotuner: for each order, times n_trials RK steps with every built tile shape
+ * (elements per CTA) of the FP32 kernels on this batch's own meshes, keeps the fastest and drops
+ * the captured graph.  Q and workspace are scratch (their contents are overwritten).  choice: host
+ * int[4] receiving the chosen elements per CTA for p = 2..5 (0 where the order is absent), or NULL.
+ * Synchronises. */
+chorus_status chorus_batch_autotune(chorus_batch batch, float* Q, void* workspace, double dt, int n_trials,
+                                    void* stream, int* choice);
+
 /* Synchronise the stream and report a pending device-side error flag (CHORUS_ETIMEOUT). */
 chorus_status chorus_check(chorus_mesh mesh, void* stream);
 

@@ -6,7 +6,7 @@ cubed-sphere inputs.
 """
 from __future__ import annotations
 
-from .native import FP32_PERT, FP64, ChorusError, Mesh, Params, load, max_sound_speed, stable_dt  # noqa: F401
+from .native import FP32_PERT, FP64, Batch, ChorusError, Mesh, Params, load, max_sound_speed, stable_dt  # noqa: F401
 
 
 class Shell:
@@ -23,3 +23,23 @@ class Shell:
         self.h_min = info["h_min"]
         ph = cfg.phys
         self.dt = stable_dt(cfg.p, self.h_min, max_sound_speed(ph, cfg.r_inner, cfg.r_outer), max(ph.nu, ph.kappa))
+
+
+class Shells:
+    """A batch of independent shells on the GPU (see chorus_batch_create) with one common stable
+    time step: the smallest of the orders' steps by the single-shell rule."""
+
+    def __init__(self, bcfg, stream=None):
+        from chorus_inputs import cubed_sphere_hex20
+
+        self.bcfg = bcfg
+        self.cfgs = bcfg.shells()
+        shells = []
+        for c in self.cfgs:
+            xyz, h20 = cubed_sphere_hex20(c.n, c.n_r, c.r_inner, c.r_outer)
+            shells.append((xyz, h20, c.p, c.seed, c.entropy_amp))
+        self.params = Params.from_phys(bcfg.phys)
+        self.batch = Batch(shells, bcfg.r_inner, bcfg.r_outer, self.params, stream)
+        ph = bcfg.phys
+        c = max_sound_speed(ph, bcfg.r_inner, bcfg.r_outer)
+        self.dt = min(stable_dt(p, h, c, max(ph.nu, ph.kappa)) for p, h in self.batch.group_h_min.items())

@@ -12,51 +12,11 @@
 #include "closure.h"
 #include "internal.h"
 #include "mesh_builder.h"
+#include "mesh_state.h"
 #include "sd_tables.h"
 
 using namespace chorus;
 
-struct chorus_mesh_s {
-  int p = 0, N = 0;
-  int64_t E = 0;
-  double r_inner = 0, r_outer = 0;
-  HostMesh host;
-  Tables1D tab;
-  LaunchSet L{};
-  OpsArg<double> ops64{};
-  OpsArg<float> ops32{};
-  // device mesh arrays
-  int* d_nbr = nullptr;
-  int* d_code = nullptr;
-  double* d_Sf64 = nullptr;
-  double* d_invJ64 = nullptr;
-  double* d_x64 = nullptr;
-  double* d_wJ = nullptr;  // w_i w_j w_k |J| at the solution points (reductions)
-  float* d_Sf32 = nullptr;
-  float* d_invJ32 = nullptr;
-  float* d_x32 = nullptr;
-  unsigned* d_err = nullptr;
-  // prepared background
-  bool prepared = false;
-  chorus_params prep{};
-  double* d_Q0 = nullptr;     // [E][5][N3] FP64 polytrope at rest
-  float* d_bg = nullptr;      // [E][2][N3]
-  float* d_grho0 = nullptr;   // [E][3][N3]
-  float* d_bgT = nullptr;     // [E][6][2][N2]
-  float* d_R0 = nullptr;      // [E][5][N3]
-  double* d_red = nullptr;    // reduction partials
-  // measurement: event pairs around launches while timing is enabled
-  struct Rec {
-    int cls;
-    cudaEvent_t a, b;
-  };
-  bool timing = false;
-  std::vector<Rec> recs;
-  std::vector<cudaEvent_t> pool;
-  // attached learned closure (p = 2 meshes): record pointer and its per-stage output buffer
-  const void* closure = nullptr;
-  void* closure_buf = nullptr;
-};
 
 namespace {
 
@@ -430,6 +390,15 @@ bool same_params(const chorus_params& a, const chorus_params& b) {
 
 inline dim3 grid1(int64_t n, int bs = 256) { return dim3((unsigned)((n + bs - 1) / bs)); }
 
+LaunchSet launchers_for(int p, int tile) {
+  switch (p) {
+    case 2: return launchers_p2(tile);
+    case 3: return launchers_p3(tile);
+    case 4: return launchers_p4(tile);
+    default: return launchers_p5(tile);
+  }
+}
+
 }  // namespace
 
 extern "C" {
@@ -467,12 +436,7 @@ chorus_status chorus_mesh_create(int64_t n_nodes, const double* node_xyz, int64_
     delete m;
     return (chorus_status)rc;
   }
-  switch (p) {
-    case 2: m->L = launchers_p2(); break;
-    case 3: m->L = launchers_p3(); break;
-    case 4: m->L = launchers_p4(); break;
-    default: m->L = launchers_p5(); break;
-  }
+  m->L = launchers_for(p, 0);
   fill_ops(m->tab, &m->ops64);
   fill_ops(m->tab, &m->ops32);
   const int N = m->N, N2 = N * N, N3 = N2 * N;
@@ -1036,3 +1000,50 @@ extern "C" chorus_status chorus_residual_noalloc(chorus_mesh m, const chorus_par
                    kModeResidual, m->d_err, st));
   return CHORUS_OK;
 }
+
+// ---------------------------------------------------------------- calls of the batched-shell layer
+
+namespace chorus {
+
+chorus_status mesh_init_range(chorus_mesh_s* m, uint64_t seed, double amp, float* Q, int64_t e0, int64_t ne,
+                              cudaStream_t st) {
+  if (!m || !Q || !m->prepared || e0 < 0 || ne < 0 || e0 + ne > m->E || !(amp >= 0.0 && amp < 1.0))
+    return CHORUS_EINVAL;
+  if (ne == 0) return CHORUS_OK;
+  const int N3 = m->N * m->N * m->N;
+  const int64_t nP = ne * N3;
+  const size_t off = (size_t)e0 * 5 * N3;
+  k_init<<<grid1(nP), 256, 0, st>>>(nP, N3, m->d_Q0 + off, seed, amp, 1, nullptr, Q + off);
+  return cu(cudaGetLastError());
+}
+
+chorus_status mesh_reduce_range(chorus_mesh_s* m, const float* Q, int64_t e0, int64_t ne, double out[4],
+                                cudaStream_t st) {
+  if (!m || !Q || !out || !m->prepared || e0 < 0 || ne < 0 || e0 + ne > m->E) return CHORUS_EINVAL;
+  const int N3 = m->N * m->N * m->N;
+  const int64_t nP = ne * N3;
+  const size_t off5 = (size_t)e0 * 5 * N3, off1 = (size_t)e0 * N3;
+  k_reduce_partial<float><<<kRedBlocks, 256, 0, st>>>(nP, N3, Q + off5, m->d_Q0 + off5, m->d_wJ + off1,
+                                                      m->d_x64 + 3 * off1, m->d_red);
+  k_reduce_final<<<1, 32, 0, st>>>(kRedBlocks, m->d_red, m->d_red + kRedBlocks * 6);
+  CHK(cudaGetLastError());
+  double r[6];
+  CHK(cudaMemcpyAsync(r, m->d_red + kRedBlocks * 6, sizeof(r), cudaMemcpyDeviceToHost, st));
+  CHK(cudaStreamSynchronize(st));
+  out[0] = r[0];
+  out[1] = r[1];
+  out[2] = r[2];
+  out[3] = std::sqrt(r[3] * r[3] + r[4] * r[4] + r[5] * r[5]);
+  for (int i = 0; i < 4; ++i)
+    if (!std::isfinite(out[i])) return CHORUS_ENAN;
+  return CHORUS_OK;
+}
+
+int mesh_set_tile(chorus_mesh_s* m, int tile) {
+  if (!m || tile < 0 || tile >= kTiles) return -1;
+  m->L = launchers_for(m->p, tile);
+  m->tile = tile;
+  return m->L.epb32;
+}
+
+}  // namespace chorus

@@ -79,11 +79,15 @@ struct LaunchSet {
   cudaError_t (*resid32)(const MeshArg<float>&, const OpsArg<float>&, const PhysArg<float>&, const BgArg&,
                          const float* q, const float* T, const float* Tv, const float* G, float* out, float* T_out,
                          const RkCoef<float>& rk, float dt, int mode, unsigned* err, cudaStream_t);
+  int epb32;  // elements per CTA of the FP32 kernels
 };
 
-LaunchSet launchers_p2();
-LaunchSet launchers_p3();
-LaunchSet launchers_p4();
-LaunchSet launchers_p5();
+// Each order is built with kTiles tile shapes of its FP32 kernels (elements per CTA); tile 0 is
+// the default, the others are candidates for the batched-shell autotuner.  FP64 kernels have one.
+constexpr int kTiles = 2;
+LaunchSet launchers_p2(int tile);
+LaunchSet launchers_p3(int tile);
+LaunchSet launchers_p4(int tile);
+LaunchSet launchers_p5(int tile);
 
 }  // namespace chorus

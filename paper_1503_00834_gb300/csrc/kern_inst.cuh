@@ -60,7 +60,7 @@ struct Inst {
     A.dt = dt; A.err = err;
     return mode == kModeRK ? L32::template resid<kModeRK>(A, st) : L32::template resid<kModeResidual>(A, st);
   }
-  static LaunchSet set() { return LaunchSet{trace64, grad64, resid64, trace32, grad32, resid32}; }
+  static LaunchSet set() { return LaunchSet{trace64, grad64, resid64, trace32, grad32, resid32, EPB32}; }
 };
 
 }  // namespace chorus

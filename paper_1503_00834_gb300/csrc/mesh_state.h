@@ -1,0 +1,72 @@
+// The mesh handle behind chorus_mesh and the internal calls that the batched-shell layer
+// (batch.cu) makes on it.
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <vector>
+
+#include "chorus.h"
+#include "internal.h"
+#include "mesh_builder.h"
+#include "sd_tables.h"
+
+struct chorus_mesh_s {
+  int p = 0, N = 0;
+  int64_t E = 0;
+  double r_inner = 0, r_outer = 0;
+  chorus::HostMesh host;
+  chorus::Tables1D tab;
+  chorus::LaunchSet L{};
+  int tile = 0;  // FP32 tile shape in use (index into the order's built tile shapes)
+  chorus::OpsArg<double> ops64{};
+  chorus::OpsArg<float> ops32{};
+  // device mesh arrays
+  int* d_nbr = nullptr;
+  int* d_code = nullptr;
+  double* d_Sf64 = nullptr;
+  double* d_invJ64 = nullptr;
+  double* d_x64 = nullptr;
+  double* d_wJ = nullptr;  // w_i w_j w_k |J| at the solution points (reductions)
+  float* d_Sf32 = nullptr;
+  float* d_invJ32 = nullptr;
+  float* d_x32 = nullptr;
+  unsigned* d_err = nullptr;
+  // prepared background
+  bool prepared = false;
+  chorus_params prep{};
+  double* d_Q0 = nullptr;     // [E][5][N3] FP64 polytrope at rest
+  float* d_bg = nullptr;      // [E][2][N3]
+  float* d_grho0 = nullptr;   // [E][3][N3]
+  float* d_bgT = nullptr;     // [E][6][2][N2]
+  float* d_R0 = nullptr;      // [E][5][N3]
+  double* d_red = nullptr;    // reduction partials
+  // measurement: event pairs around launches while timing is enabled
+  struct Rec {
+    int cls;
+    cudaEvent_t a, b;
+  };
+  bool timing = false;
+  std::vector<Rec> recs;
+  std::vector<cudaEvent_t> pool;
+  // attached learned closure (p = 2 meshes): record pointer and its per-stage output buffer
+  const void* closure = nullptr;
+  void* closure_buf = nullptr;
+};
+
+namespace chorus {
+
+// Seeded perturbation (as chorus_state_init, FP32 form) of elements [e0, e0 + ne) of a prepared
+// mesh, indexing the points from the range's first point, so that the range gets the state a
+// standalone mesh of those elements gets.
+chorus_status mesh_init_range(chorus_mesh_s* m, uint64_t seed, double amp, float* Q, int64_t e0, int64_t ne,
+                              cudaStream_t st);
+
+// chorus_reduce (FP32 form) over elements [e0, e0 + ne).  Synchronises.
+chorus_status mesh_reduce_range(chorus_mesh_s* m, const float* Q, int64_t e0, int64_t ne, double out[4],
+                                cudaStream_t st);
+
+// Select the FP32 tile shape `tile` (0 <= tile < n_tiles(p)); returns the elements per CTA or -1.
+int mesh_set_tile(chorus_mesh_s* m, int tile);
+
+}  // namespace chorus

@@ -28,7 +28,9 @@ EXPORTS = ("chorus_mesh_create", "chorus_mesh_destroy", "chorus_mesh_info", "cho
            "chorus_strerror", "chorus_timing_enable", "chorus_timing_read", "chorus_residual_noalloc",
            "chorus_am_correct", "chorus_rk_step_scheme", "chorus_closure_bytes", "chorus_closure_init",
            "chorus_project", "chorus_closure_forward", "chorus_closure_grad", "chorus_closure_make_pairs",
-           "chorus_closure_train", "chorus_closure_apply", "chorus_closure_attach")
+           "chorus_closure_train", "chorus_closure_apply", "chorus_closure_attach", "chorus_batch_create",
+           "chorus_batch_destroy", "chorus_batch_layout", "chorus_batch_init", "chorus_batch_rk_step",
+           "chorus_batch_reduce", "chorus_batch_autotune")
 
 
 class ChorusError(RuntimeError):
@@ -43,6 +45,14 @@ class TrainCfg(ctypes.Structure):
     _fields_ = [("epochs", ctypes.c_int64), ("batch", ctypes.c_int64), ("lr", ctypes.c_double),
                 ("beta1", ctypes.c_double), ("beta2", ctypes.c_double), ("eps", ctypes.c_double),
                 ("seed", ctypes.c_uint64)]
+
+
+class ShellDesc(ctypes.Structure):
+    """chorus_shell_desc."""
+
+    _fields_ = [("n_nodes", ctypes.c_int64), ("node_xyz", ctypes.POINTER(ctypes.c_double)),
+                ("n_elem", ctypes.c_int64), ("hex20", ctypes.POINTER(ctypes.c_int64)), ("p", ctypes.c_int),
+                ("seed", ctypes.c_uint64), ("entropy_amp", ctypes.c_double)]
 
 
 class Params(ctypes.Structure):
@@ -95,6 +105,13 @@ def load() -> ctypes.CDLL:
         "chorus_closure_train": (i32, [vp, vp, i64, vp, P(TrainCfg), P(f64), vp]),
         "chorus_closure_apply": (i32, [vp, i32, vp, vp, vp, vp]),
         "chorus_closure_attach": (i32, [vp, vp]),
+        "chorus_batch_create": (i32, [i32, P(ShellDesc), f64, f64, P(Params), vp, P(vp)]),
+        "chorus_batch_destroy": (i32, [vp]),
+        "chorus_batch_layout": (i32, [vp, P(i64), P(i64), P(ctypes.c_size_t), P(i32), P(i32), P(f64)]),
+        "chorus_batch_init": (i32, [vp, vp, vp]),
+        "chorus_batch_rk_step": (i32, [vp, vp, vp, f64, i64, vp, P(i64)]),
+        "chorus_batch_reduce": (i32, [vp, vp, P(f64), vp]),
+        "chorus_batch_autotune": (i32, [vp, vp, vp, f64, i32, vp, P(i32)]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(lib, name)
@@ -210,6 +227,86 @@ class Mesh:
 
     def check(self, stream=None) -> None:
         _ok("chorus_check", load().chorus_check(self.handle, _stream(stream)))
+
+
+# ---------------------------------------------------------------- batched independent shells
+
+
+class Batch:
+    """Independent shells of several orders advanced together (chorus_batch handle).
+
+    shells: sequence of (node_xyz, hex20, p, seed, entropy_amp).  The FP32 perturbation state of
+    every shell lives in one device array; `view(Q, s)` is shell s's [E][5][N^3] block.
+    """
+
+    def __init__(self, shells, r_inner: float, r_outer: float, params: Params, stream=None):
+        lib = load()
+        self._keep = []
+        descs = (ShellDesc * len(shells))()
+        self.orders, self.n_elem = [], []
+        for i, (xyz, h20, p, seed, amp) in enumerate(shells):
+            xyz = np.ascontiguousarray(xyz, dtype=np.float64)
+            h20 = np.ascontiguousarray(h20, dtype=np.int64)
+            self._keep += [xyz, h20]
+            descs[i] = ShellDesc(xyz.shape[0], xyz.ctypes.data_as(ctypes.POINTER(ctypes.c_double)), h20.shape[0],
+                                 h20.ctypes.data_as(ctypes.POINTER(ctypes.c_int64)), p, seed, amp)
+            self.orders.append(p)
+            self.n_elem.append(h20.shape[0])
+        handle = ctypes.c_void_p()
+        _ok("chorus_batch_create", lib.chorus_batch_create(len(shells), descs, r_inner, r_outer,
+                                                           ctypes.byref(params), _stream(stream), ctypes.byref(handle)))
+        self._keep = []
+        self.handle = handle
+        self.params = params
+        off = (ctypes.c_int64 * len(shells))()
+        n_state, ws, ng = ctypes.c_int64(), ctypes.c_size_t(), ctypes.c_int()
+        gp, gh = (ctypes.c_int * 4)(), (ctypes.c_double * 4)()
+        _ok("chorus_batch_layout", lib.chorus_batch_layout(handle, off, ctypes.byref(n_state), ctypes.byref(ws),
+                                                           ctypes.byref(ng), gp, gh))
+        self.offsets = list(off)
+        self.n_state, self.workspace_bytes, self.n_groups = n_state.value, ws.value, ng.value
+        self.group_h_min = {gp[g]: gh[g] for g in range(ng.value)}  # order -> shortest edge chord
+
+    def close(self) -> None:
+        if getattr(self, "handle", None) and self.handle.value:
+            load().chorus_batch_destroy(self.handle)
+            self.handle = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def n_dof(self) -> int:
+        return sum(e * (p + 1) ** 3 for e, p in zip(self.n_elem, self.orders))
+
+    def view(self, Q, s: int):
+        N3 = (self.orders[s] + 1) ** 3
+        o = self.offsets[s]
+        return Q[o:o + self.n_elem[s] * 5 * N3].view(self.n_elem[s], 5, N3)
+
+    def init(self, Q, stream=None) -> None:
+        _ok("chorus_batch_init", load().chorus_batch_init(self.handle, _ptr(Q), _stream(stream)))
+
+    def rk_step(self, Q, ws, dt: float, n_steps: int, stream=None) -> int:
+        """n_steps SSP-RK3 steps (graph replay); returns the kernel launches per step."""
+        n = ctypes.c_int64()
+        _ok("chorus_batch_rk_step", load().chorus_batch_rk_step(self.handle, _ptr(Q), _ptr(ws), dt, n_steps,
+                                                                _stream(stream), ctypes.byref(n)))
+        return n.value
+
+    def reduce(self, Q, stream=None) -> np.ndarray:
+        out = (ctypes.c_double * (4 * len(self.orders)))()
+        _ok("chorus_batch_reduce", load().chorus_batch_reduce(self.handle, _ptr(Q), out, _stream(stream)))
+        return np.array(out[:]).reshape(-1, 4)
+
+    def autotune(self, Q, ws, dt: float, n_trials: int = 3, stream=None):
+        """Chosen elements per CTA for p = 2..5 (0 where absent)."""
+        ch = (ctypes.c_int * 4)()
+        _ok("chorus_batch_autotune", load().chorus_batch_autotune(self.handle, _ptr(Q), _ptr(ws), dt, n_trials,
+                                                                  _stream(stream), ch))
+        return list(ch)
 
 
 # ---------------------------------------------------------------- learned closure

@@ -145,6 +145,39 @@ def test_rk_steps_match_oracle(prec):
         assert e < 1e-5
 
 
+@pytest.mark.parametrize("prec", [0, 1], ids=["fp64", "fp32pert"])
+@pytest.mark.parametrize("p", [2, 4, 5])
+def test_rk_steps_match_oracle_other_orders(p, prec):
+    """RK mode (stage combination, next-stage traces) of the p = 2, 4, 5 kernels: 10 SSP-RK3 steps
+    of a 24-element shell, same tolerances as the p = 3 trajectory test."""
+    from oracle import rk
+    from oracle.residual import residual
+    from paper_1503_00834_gb300 import FP64
+
+    cfg = small_shell(2, 1, p)
+    n_steps = 10
+    sh = _gpu(cfg)
+    osh = OracleShell(cfg)
+    Q = _alloc(sh.mesh, prec)[0]
+    sh.mesh.state_init(sh.params, cfg.seed, cfg.entropy_amp, prec, Q)
+    sh.mesh.rk_step(sh.params, prec, Q, _ws(sh.mesh, prec), sh.dt, n_steps)
+    sh.mesh.check()
+    Qinit = osh.initial_state()
+    Qref = rk.run(osh.disc, osh.ph, Qinit, sh.dt, n_steps)
+    Q0 = osh.background()
+    W = osh.weights()
+    got = to5(Q, p + 1) - (Q0 if prec == FP64 else 0.0)
+    e, ev = rel_err(got, Qref - Q0, W)
+    print(f"p={p} rk {n_steps} steps prec {prec}: rel err on q' {ev}")
+    if prec == FP64:
+        noisy = _noisy_run(osh, Qinit, sh.dt, n_steps)
+        _, spread = rel_err(noisy - Q0, Qref - Q0, W)
+        kappa = _condition(osh, Qinit, residual(osh.disc, osh.ph, Qinit), W)
+        assert np.all(ev <= np.maximum(1e-12 * np.maximum(1.0, kappa), 10.0 * spread))
+    else:
+        assert e < 1e-5
+
+
 def _noisy_run(osh, Q, dt, n_steps):
     """Oracle SSP-RK3 with a relative 2^-53 random perturbation of the state after every stage."""
     from oracle.residual import residual
