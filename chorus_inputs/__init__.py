@@ -261,3 +261,36 @@ def small_batch() -> BatchConfig:
     """A small batch of the same family for tests (every order, ragged sizes)."""
     return BatchConfig("batch_small", 6, 9, 1, 3, 1, 3, (2, 3, 4, 5), 0.75, 1.0, 1e-3,
                        make_phys(0.75, 1.5, 3.0, 1e-3))
+
+
+# ---- the paper's benchmark parameter sets (Tables 1 and 2), in this package's units
+# Units: length R_o, GM = 1 (time sqrt(R_o^3 / GM)), density rho_c = the polytrope's mid-layer density
+# (rho_i / chi_i^n), gas constant 1.  A dimensional kinematic coefficient k becomes k t_u / R_o^2,
+# a rate W becomes W t_u, a luminosity L becomes L t_u^3 / (rho_c R_o^5).
+_G_CGS = 6.67e-8
+PAPER_CASES = {
+    # Table 1 (Jupiter benchmark): kappa_r = 0
+    "jupiter": dict(beta=0.35, n=2.0, N_rho=5.0, R_o=7.0e9, Omega=1.76e-4, M=1.9e30, rho_i=1.1, nu=3.64364e12,
+                    kappa=3.64364e12, L=7.014464e32),
+    # Table 2 (solar benchmark); its radiative diffusion profile kappa_r(r) is not modelled (kappa_r = 0)
+    "sun": dict(beta=0.736762, n=1.5, N_rho=3.0, R_o=6.61e10, Omega=8.1e-5, M=1.98891e33, rho_i=0.21, nu=6.0e13,
+                kappa=6.0e13, L=3.846e36),
+}
+
+
+def paper_case_phys(name: str) -> tuple:
+    """(beta, PhysParams) of a Table 1/2 case; bottom_flux = L / (4 pi r_i^2), T_top left NaN (the
+    caller sets it from the stratification it uses)."""
+    c = PAPER_CASES[name]
+    beta, n = c["beta"], c["n"]
+    t_u = math.sqrt(c["R_o"] ** 3 / (_G_CGS * c["M"]))
+    chi_o = (beta + 1.0) / (beta * math.exp(c["N_rho"] / n) + 1.0)
+    chi_i = (1.0 + beta - chi_o) / beta
+    rho_c = c["rho_i"] / chi_i ** n
+    L = c["L"] * t_u ** 3 / (rho_c * c["R_o"] ** 5)
+    nu = c["nu"] * t_u / c["R_o"] ** 2
+    kappa = c["kappa"] * t_u / c["R_o"] ** 2
+    phys = PhysParams(gamma=1.0 + 1.0 / n, R_gas=1.0, GM=1.0, Omega=c["Omega"] * t_u, nu=nu, kappa=kappa, kappa_r=0.0,
+                      poly_n=n, N_rho=c["N_rho"], rho_c=1.0, bottom_flux=L / (4.0 * math.pi * beta * beta),
+                      T_top=float("nan"))
+    return beta, phys

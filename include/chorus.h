@@ -97,7 +97,31 @@ chorus_status chorus_mesh_info(chorus_mesh mesh, int64_t* n_dof, int64_t* n_face
  * rebuilds them.  Allocates device memory owned by the mesh handle. */
 chorus_status chorus_prepare(chorus_mesh mesh, const chorus_params* params, void* stream);
 
-/* Seeded initial state (Section 4): the polytrope at rest with an entropy perturbation
+/* Background from a radial profile instead of the polytrope: rho0, p0 host double[n] (n >= 4) on the
+ * uniform grid r_j = r0 + j (r1 - r0)/(n - 1), at rest; the solution-point values come from cubic
+ * Lagrange interpolation on the four nearest nodes.  The grid must cover the radii of all solution
+ * points - 20-node elements can place some slightly outside the spherical walls, so take a margin
+ * of a few percent of the shell thickness - and be fine enough that the interpolation error is
+ * negligible (16,385 nodes give about 1e-15 relative for the workloads).  Builds the same tables as
+ * chorus_prepare; a later chorus_prepare with the same params keeps this background.  Non-positive
+ * or non-finite entries, n < 4 or r1 <= r0 > 0: CHORUS_EINVAL.  Synchronises. */
+chorus_status chorus_prepare_profile(chorus_mesh mesh, const chorus_params* params, int64_t n, double r0, double r1,
+                                     const double* rho0, const double* p0, void* stream);
+
+/* The almost-flux-balance stratification of Section 4.3 on the uniform grid above (host; no GPU):
+ * target entropy gradient Gamma(r) = -(L/(4 pi r^2) + rho_a C_p kappa_r dT_a/dr) / (rho_a T_a kappa)
+ * (the thermal balance of Section 4.1 integrated with outward luminosity L; superadiabatic)
+ * with L = 4 pi r_inner^2 bottom_flux and the polytrope rho_a, T_a of params and the shell radii,
+ * then drho0/dr = -rho0 (Gamma/C_p + g rho0/(gamma p0)), dp0/dr = -rho0 g (g = GM/r^2), integrated
+ * with classical RK4 (16 substeps per grid interval) outward and inward from the middle radius
+ * (r_inner + r_outer)/2, where rho0 and p0 take the polytrope's values (the paper starts its solve
+ * from the polytrope; the anchoring point is this library's reading).  The grid [r0, r1] may extend
+ * beyond the walls (the equations continue there).  n >= 2, kappa > 0; rho0, p0: host double[n]
+ * outputs.  CHORUS_ENAN if the stratification leaves positive density or pressure. */
+chorus_status chorus_afb_profile(const chorus_params* params, double r_inner, double r_outer, double r0, double r1,
+                                 int64_t n, double* rho0, double* p0);
+
+/* Seeded initial state (Section 4): the prepared background at rest with an entropy perturbation
  * S'/C_p = A xi, xi in [-1,1) from SplitMix64(seed XOR g) at global solution point
  * g = e N^3 + (i + N j + N^2 k); pressure kept, rho = rho_a exp(-A xi).  Q: device, layout above,
  * in the given precision (total state for FP64, perturbation for FP32_PERT). */
@@ -156,6 +180,10 @@ size_t chorus_closure_bytes(void);
 chorus_status chorus_closure_init(void* weights, uint64_t seed, const float* in_scale, const float* out_scale,
                                   void* stream);
 
+/* Overwrite the input and output scales of a record (host float[5] each, > 0), keeping its weights:
+ * scaling out_scale by a factor relaxes the correction.  Synchronises the stream. */
+chorus_status chorus_closure_set_scales(void* weights, const float* in_scale, const float* out_scale, void* stream);
+
 /* Per-element L2 projection from `fine` to `coarse` (same elements, lower order) in the reference
  * cube, one direction at a time (P = M_c^-1 B with exact Gauss-Legendre integrals).  kind 0: a
  * state in the given precision (for FP32_PERT the fine background is added before and the coarse
@@ -164,8 +192,15 @@ chorus_status chorus_closure_init(void* weights, uint64_t seed, const float* in_
 chorus_status chorus_project(chorus_mesh fine, chorus_mesh coarse, chorus_precision prec, int kind, const void* Qf,
                              void* Qc, void* stream);
 
-/* Network forward pass on n samples: X, Y device [n][135] FP32. */
+/* Network forward pass on n samples: X, Y device [n][135] FP32, FP32 activations (the training
+ * arithmetic). */
 chorus_status chorus_closure_forward(const void* weights, const float* X, float* Y, int64_t n, void* stream);
+
+/* The same forward pass on the tensor cores (tcgen05, 128-sample tiles, persistent CTAs): each
+ * layer's input is rounded to BF16 (nearest even), products accumulate in FP32, bias and SiLU in
+ * FP32.  This is the arithmetic of the closure inside the residual and the RK stages
+ * (chorus_closure_apply / chorus_closure_attach). */
+chorus_status chorus_closure_forward_tc(const void* weights, const float* X, float* Y, int64_t n, void* stream);
 
 /* Gradient of L = sum (y - t)^2 / (2 * 135 n) with respect to the parameters (FP32 device vector of
  * W1, W2, W3, b1, b2, b3 in that order, 51,335 entries, overwritten) and the loss (host).
@@ -213,12 +248,12 @@ chorus_status chorus_timing_read(chorus_mesh mesh, void* stream, double* ms, int
  * counterpart: this is a library convenience.  Some callers cannot allocate device memory when they
  * need a residual - for example an application that has handed all device memory to its own pool
  * allocator, or a latency-critical loop that must not call cudaMalloc (which can synchronise the
- * device).  They pass only the state Q and the output R (device, layout above); the face-trace
- * scratch lives in one fixed 32 MiB device array inside the library, which every GPU that loads the
- * library holds until the process exits.
- *  - Size limit: E * 6 * 9 * N^2 words of the chosen precision must fit in 32 MiB (FP32 p = 3:
- *    up to 9,709 elements; FP64 p = 3: up to 4,854).  Larger meshes return CHORUS_EINVAL before any
- *    launch; use chorus_residual with a workspace for them.
+ * device).  They pass only the state Q and the output R (device, layout above); the scratch (face
+ * traces, one-sided viscous face fluxes, gradient record) lives in one fixed 32 MiB device array
+ * inside the library, which every GPU that loads the library holds until the process exits.
+ *  - Size limit: E * (6 * 9 * N^2 + 12 * N^3) words of the chosen precision must fit in 32 MiB
+ *    (FP32 p = 3: up to 5,140 elements; FP64 p = 3: up to 2,570).  Larger meshes return
+ *    CHORUS_EINVAL before any launch; use chorus_residual with a workspace for them.
  *  - Set-up: the first call on a device looks up the array's device address with that device
  *    current; make that first call before any stream capture.  Call with the mesh's device current.
  *  - Sharing: all calls share the one array and it keeps the previous call's contents (every call
@@ -287,6 +322,15 @@ chorus_status chorus_batch_reduce(chorus_batch batch, const float* Q, double* ou
  * Synchronises. */
 chorus_status chorus_batch_autotune(chorus_batch batch, float* Q, void* workspace, double dt, int n_trials,
                                     void* stream, int* choice);
+
+/* Well-balanced perturbation residual (FP32_PERT only; a library option the paper has no
+ * counterpart for).  The residual of Q0 + q' becomes R(Q0 + q') - R(Q0): the discrete residual of the
+ * polytropic background at rest, which is not zero but of truncation size (the discretised
+ * hydrostatic balance, Section 4), is left out, so the background is an exact steady state and q'
+ * evolves only under its own dynamics.  Used to compare runs of different orders, whose background
+ * truncation errors differ.  enable = 0 restores the plain residual.  Applies to chorus_residual and
+ * chorus_rk_step / chorus_rk_step_scheme in the FP32 perturbation form. */
+chorus_status chorus_set_well_balanced(chorus_mesh mesh, int enable);
 
 /* Synchronise the stream and report a pending device-side error flag (CHORUS_ETIMEOUT). */
 chorus_status chorus_check(chorus_mesh mesh, void* stream);

@@ -66,6 +66,26 @@ def forward(params, X):
     return Y, dict(X=X, z1=z1, h1=h1, z2=z2, h2=h2)
 
 
+def round_bf16(x):
+    """Round to the nearest bfloat16 value (8-bit significand, ties to even), returned as float64.
+
+    bfloat16 keeps the sign, the 8 exponent bits and the top 7 fraction bits of an IEEE binary32.
+    The value is first rounded to binary32, then the low 16 bits are rounded off: add 0x7FFF plus
+    the lowest kept bit and truncate (round half to even on the dropped 16 bits)."""
+    b = np.ascontiguousarray(np.asarray(x, dtype=np.float32)).view(np.uint32).astype(np.uint64)
+    keep = (b >> np.uint64(16)) & np.uint64(1)
+    r = ((b + np.uint64(0x7FFF) + keep) >> np.uint64(16)) << np.uint64(16)
+    return r.astype(np.uint32).view(np.float32).astype(np.float64)
+
+
+def forward_bf16_inputs(params, X):
+    """The forward pass with every layer's input rounded to bfloat16 (the tensor-core arithmetic:
+    BF16 operands, sums in a wider format)."""
+    z1 = round_bf16(X) @ params["W1"].T + params["b1"]
+    z2 = round_bf16(silu(z1)) @ params["W2"].T + params["b2"]
+    return round_bf16(silu(z2)) @ params["W3"].T + params["b3"]
+
+
 def loss_and_grad(params, X, T):
     """Mean squared error / 2 and its gradient with respect to every parameter (backpropagation)."""
     Y, c = forward(params, X)

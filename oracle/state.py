@@ -45,15 +45,16 @@ def background(ph: Physics, x: np.ndarray) -> np.ndarray:
     return Q0
 
 
-def initial_state(ph: Physics, x: np.ndarray, seed: int, amp: float, elems=None) -> np.ndarray:
-    """Initial state at the solution points x [E,3,N,N,N] of elements `elems` (default 0..E-1)."""
+def initial_state(ph: Physics, x: np.ndarray, seed: int, amp: float, elems=None, Q0=None) -> np.ndarray:
+    """Initial state at the solution points x [E,3,N,N,N] of elements `elems` (default 0..E-1), on
+    the polytropic background or on the given background Q0 (same shape as the state)."""
     E = x.shape[0]
     N = x.shape[2]
     elems = np.arange(E) if elems is None else np.asarray(elems)
     g = (elems.astype(np.uint64)[:, None, None, None] * np.uint64(N ** 3)
          + np.arange(N ** 3, dtype=np.uint64).reshape(N, N, N)[None])
     xi = uniform_pm1(seed, g)
-    Q = background(ph, x)
+    Q = background(ph, x) if Q0 is None else np.array(Q0, dtype=np.float64)
     Q[:, 0] = Q[:, 0] * np.exp(-amp * xi)
     return Q
 
@@ -66,12 +67,15 @@ def min_edge_chord(node_xyz: np.ndarray, hex20: np.ndarray) -> float:
 
 
 def time_step(ph: Physics, p: int, h_min: float, Q: np.ndarray) -> float:
-    """Fixed explicit step: 0.5 h/((2p+1) max(|u|+c)), capped by 0.25 h^2/((2p+1)^2 max(nu, kappa))."""
+    """Fixed explicit step: 0.25 h/((2p+1) max(|u|+c)), capped by 0.25 h^2/((2p+1)^2 max(nu, kappa)).
+
+    The paper states only a CFL condition (Section 7); h/((2p+1) c) is the one-dimensional limit,
+    shared among the three directions of an element with comparable edges (factor 0.25 < 1/3)."""
     rho = Q[:, 0]
     u2 = (Q[:, 1] ** 2 + Q[:, 2] ** 2 + Q[:, 3] ** 2) / rho ** 2
     pres = (ph.gamma - 1.0) * (Q[:, 4] - 0.5 * rho * u2)
     wave = float(np.max(np.sqrt(u2) + np.sqrt(ph.gamma * pres / rho)))
-    dt = 0.5 * h_min / ((2 * p + 1) * wave)
+    dt = 0.25 * h_min / ((2 * p + 1) * wave)
     diff = max(ph.nu, ph.kappa)
     if diff > 0:
         dt = min(dt, 0.25 * h_min * h_min / ((2 * p + 1) ** 2 * diff))

@@ -20,7 +20,7 @@ INCLUDE = os.path.join(os.path.dirname(HERE), "include")
 
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 NVFLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-I", CSRC, "-I", INCLUDE]
-SOURCES = ["capi.cu", "batch.cu", "closure.cu", "kern_p2.cu", "kern_p3.cu", "kern_p4.cu", "kern_p5.cu", "mesh_builder.cpp"]
+SOURCES = ["capi.cu", "batch.cu", "closure.cu", "closure_tc.cu", "kern_p2.cu", "kern_p3.cu", "kern_p4.cu", "kern_p5.cu", "mesh_builder.cpp"]
 
 
 def _nvcc() -> str:

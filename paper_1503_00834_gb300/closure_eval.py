@@ -4,12 +4,14 @@ Procedure (every step runs in the library's kernels; this module only orders the
 computes the two error diagnostics on the host):
   1. A seeded p = 5 run with FP32 perturbation storage and SSP-RK3 at the common step
      dt = min(dt_5, dt_2).  Its projection to p = 2 (per-element L2 projection) at every checkpoint
-     is the reference trajectory.
+     is the reference trajectory.  Both orders run well balanced (chorus_set_well_balanced): the
+     discrete residual of the background is left out, so each run's perturbation evolves under its
+     own dynamics and not under its order's hydrostatic truncation error.
   2. Training pairs from snapshots of the p = 5 run up to `train_until`: input the projected state,
      target P R_5(Q_5) - R_2(P Q_5) (chorus_closure_make_pairs), scaled per variable by the RMS of
      the training data; Adam on the shuffled pairs.  Snapshots after `train_until` are held out.
-  3. Plain p = 2 and closure-corrected p = 2 runs from the projected initial state, compared with
-     the reference at the checkpoints by
+  3. Plain p = 2 and closure-corrected p = 2 runs (the correction also relaxed by factors below one)
+     from the projected initial state, compared with the reference at the checkpoints by
        - the relative L2 error of the perturbation, per variable, maximum over variables, and
        - the kinetic-energy spectrum error: w = m / sqrt(rho) is expanded per element in the
          orthonormal Legendre basis of [0,1]^3 (degree <= 2 per direction); E(d) sums
@@ -91,7 +93,8 @@ class Diagnostics:
 
 
 def evaluate(steps=2000, check_every=100, snap_every=50, train_until=1000, epochs=20, batch=1024, lr=1e-3,
-             seed=11):
+             seed=11, relax=(1.0, 0.5, 0.25, 0.1)):
+    """relax: factors applied to the trained closure's output (one coarse run each)."""
     import torch
 
     from chorus_inputs import SHELL_98304_P2, SHELL_98304_P5, cubed_sphere_hex20
@@ -102,6 +105,10 @@ def evaluate(steps=2000, check_every=100, snap_every=50, train_until=1000, epoch
     fine, coarse = Shell(SHELL_98304_P5), Shell(SHELL_98304_P2)
     fine.mesh.prepare(fine.params)
     coarse.mesh.prepare(coarse.params)
+    # both orders well balanced: their background truncation residuals differ, and would otherwise
+    # drive each run's perturbation (and the closure target) more than the dynamics compared
+    fine.mesh.set_well_balanced(True)
+    coarse.mesh.set_well_balanced(True)
     dt = min(fine.dt, coarse.dt)
     cfg = fine.cfg
     f32 = dict(dtype=torch.float32, device="cuda")
@@ -190,7 +197,10 @@ def evaluate(steps=2000, check_every=100, snap_every=50, train_until=1000, epoch
     diag = Diagnostics(xyz, h20, Nc, Q0.cpu().numpy().reshape(E, 5, Nc, Nc, Nc))
     q_init = torch.tensor(ref[0].reshape(cshape), **f32)
     out = {}
-    for name, rec in (("plain", None), ("closure", w)):
+    runs = [("plain", None, 1.0)] + [(f"closure_x{a:g}", w, a) for a in relax]
+    for name, rec, a in runs:
+        if rec is not None:
+            native.closure_set_scales(rec, in_scale, [s * a for s in out_scale])
         native.closure_attach(coarse.mesh, rec)
         q = q_init.clone()
         l2, ke, ms, n = [], [], 0.0, 0
@@ -217,8 +227,8 @@ def evaluate(steps=2000, check_every=100, snap_every=50, train_until=1000, epoch
     return {
         "workload": "shell_98304: p=5 reference, p=2 plain and p=2 + learned closure",
         "dt": dt, "steps": steps, "checkpoints": list(range(0, steps + 1, check_every)),
-        "l2_plain": out["plain"]["l2"], "l2_closure": out["closure"]["l2"],
-        "ke_err_plain": out["plain"]["ke"], "ke_err_closure": out["closure"]["ke"],
+        "l2": {k: v["l2"] for k, v in out.items()},
+        "ke_err": {k: v["ke"] for k, v in out.items()},
         "ke_spectrum_ref_final": ke_ref.tolist(),
         "train": {"pairs": int(Xtr.shape[0]), "epochs": epochs, "batch": batch, "lr": lr,
                   "loss_first": losses[0], "loss_last": losses[-1], "held_out_ratio": held,
@@ -226,7 +236,7 @@ def evaluate(steps=2000, check_every=100, snap_every=50, train_until=1000, epoch
                   "snap_every": snap_every},
         "throughput": {"p5_dof_stage_per_s": cfg.n_dof * 3 * steps / max(fine_ms / 1e3, 1e-12),
                        "p2_plain_dof_stage_per_s": out["plain"]["dof_stage_per_s"],
-                       "p2_closure_dof_stage_per_s": out["closure"]["dof_stage_per_s"]},
+                       "p2_closure_dof_stage_per_s": out[runs[1][0]]["dof_stage_per_s"]},
         "seconds": {"fine_run": fine_run_s, "pairs_and_training": pairs_s, "training": train_s,
                     "total": time.perf_counter() - t_all},
     }

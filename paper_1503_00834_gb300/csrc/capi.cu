@@ -105,6 +105,34 @@ __global__ void k_background(int64_t n_pts, int N3, const double* __restrict__ x
   Qe[4 * N3 + pt] = p / (double)ph.gm1;
 }
 
+// background at rest from a radial table (uniform grid from r0 with spacing h): cubic Lagrange
+// interpolation on the four nodes around the point's radius
+__global__ void k_background_table(int64_t n_pts, int N3, const double* __restrict__ x, double r0, double h,
+                                   int64_t n_tab, const double* __restrict__ rho_t, const double* __restrict__ p_t,
+                                   double gm1, double* __restrict__ Q0) {
+  const int64_t g = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (g >= n_pts) return;
+  const int64_t e = g / N3, pt = g % N3;
+  const double x0 = x[(e * 3 + 0) * N3 + pt], x1 = x[(e * 3 + 1) * N3 + pt], x2 = x[(e * 3 + 2) * N3 + pt];
+  const double t = (sqrt(x0 * x0 + x1 * x1 + x2 * x2) - r0) / h;
+  int64_t j = (int64_t)floor(t) - 1;
+  j = j < 0 ? 0 : (j > n_tab - 4 ? n_tab - 4 : j);
+  const double s = t - (double)j;
+  const double w[4] = {-(s - 1.0) * (s - 2.0) * (s - 3.0) / 6.0, s * (s - 2.0) * (s - 3.0) / 2.0,
+                       -s * (s - 1.0) * (s - 3.0) / 2.0, s * (s - 1.0) * (s - 2.0) / 6.0};
+  double rho = 0.0, p = 0.0;
+  for (int i = 0; i < 4; ++i) {
+    rho += w[i] * rho_t[j + i];
+    p += w[i] * p_t[j + i];
+  }
+  double* Qe = Q0 + e * 5 * N3;
+  Qe[pt] = rho;
+  Qe[N3 + pt] = 0.0;
+  Qe[2 * N3 + pt] = 0.0;
+  Qe[3 * N3 + pt] = 0.0;
+  Qe[4 * N3 + pt] = p / gm1;
+}
+
 __device__ __forceinline__ uint64_t splitmix64(uint64_t x) {
   uint64_t z = x + 0x9E3779B97F4A7C15ull;
   z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
@@ -378,7 +406,9 @@ Ws<R> split_ws(const chorus_mesh_s* m, void* w) {
   return r;
 }
 
-BgArg bg_arg(const chorus_mesh_s* m) { return BgArg{m->d_bg, m->d_grho0, m->d_bgT, m->d_R0}; }
+BgArg bg_arg(const chorus_mesh_s* m) {
+  return BgArg{m->d_bg, m->d_grho0, m->d_bgT, m->well_balanced ? nullptr : m->d_R0};
+}
 
 bool same_params(const chorus_params& a, const chorus_params& b) {
   const double* x = &a.gamma;
@@ -514,11 +544,16 @@ size_t chorus_rk_workspace_bytes(chorus_mesh m, chorus_precision prec) {
   return ws_words(m) * (prec == CHORUS_FP64 ? sizeof(double) : sizeof(float)) + 256;
 }
 
-chorus_status chorus_prepare(chorus_mesh m, const chorus_params* P, void* stream) {
-  if (!m || !params_ok(P)) return CHORUS_EINVAL;
-  if (m->prepared && same_params(m->prep, *P)) return CHORUS_OK;
+}  // extern "C"
+
+namespace {
+
+// Background preparation: Q0 from the polytrope (tab == nullptr) or from a radial table of
+// rho_0, p_0 on a uniform grid over [r_inner, r_outer]; then its FP64 residual, lifted density
+// gradient and the FP32 tables of the perturbation form.
+chorus_status prepare_background(chorus_mesh_s* m, const chorus_params* P, int64_t n_tab, double r0, double r1,
+                                 const double* rho_tab, const double* p_tab, cudaStream_t st) {
   free_background(m);
-  cudaStream_t st = (cudaStream_t)stream;
   const int N = m->N, N2 = N * N, N3 = N2 * N;
   const size_t E = m->E, nP = E * N3, nT = E * 6 * 5 * N2;
   if (dev_alloc(&m->d_Q0, 5 * nP) || dev_alloc(&m->d_bg, 2 * nP) || dev_alloc(&m->d_grho0, 3 * nP) ||
@@ -526,21 +561,33 @@ chorus_status chorus_prepare(chorus_mesh m, const chorus_params* P, void* stream
     free_background(m);
     return CHORUS_ENOMEM;
   }
-  double *T = nullptr, *Tv = nullptr, *R0 = nullptr, *gr = nullptr;
-  if (dev_alloc(&T, nT) || dev_alloc(&Tv, E * 6 * 4 * N2) || dev_alloc(&R0, 5 * nP) || dev_alloc(&gr, 3 * nP)) {
-    dev_free(T); dev_free(Tv); dev_free(R0); dev_free(gr);
+  double *T = nullptr, *Tv = nullptr, *R0 = nullptr, *gr = nullptr, *tab = nullptr, *G = nullptr;
+  if (dev_alloc(&T, nT) || dev_alloc(&Tv, E * 6 * 4 * N2) || dev_alloc(&R0, 5 * nP) || dev_alloc(&gr, 3 * nP) ||
+      dev_alloc(&G, (size_t)kG * nP) || (rho_tab && dev_alloc(&tab, 2 * (size_t)n_tab))) {
+    dev_free(T); dev_free(Tv); dev_free(R0); dev_free(gr); dev_free(tab); dev_free(G);
     free_background(m);
     return CHORUS_ENOMEM;
   }
   const PhysArg<double> ph = phys_arg<double>(*P, m->r_inner, m->r_outer);
   const MeshArg<double> ma = mesh_arg<double>(m);
   cudaError_t ce = cudaSuccess;
-  k_background<<<grid1(nP), 256, 0, st>>>((int64_t)nP, N3, m->d_x64, ph, m->d_Q0);
-  ce = cudaGetLastError();
+  if (rho_tab) {
+    ce = cudaMemcpyAsync(tab, rho_tab, n_tab * sizeof(double), cudaMemcpyHostToDevice, st);
+    if (ce == cudaSuccess) ce = cudaMemcpyAsync(tab + n_tab, p_tab, n_tab * sizeof(double), cudaMemcpyHostToDevice, st);
+    if (ce == cudaSuccess) {
+      const double h = (r1 - r0) / (double)(n_tab - 1);
+      k_background_table<<<grid1(nP), 256, 0, st>>>((int64_t)nP, N3, m->d_x64, r0, h, n_tab, tab, tab + n_tab,
+                                                     P->gamma - 1.0, m->d_Q0);
+      ce = cudaGetLastError();
+    }
+  } else {
+    k_background<<<grid1(nP), 256, 0, st>>>((int64_t)nP, N3, m->d_x64, ph, m->d_Q0);
+    ce = cudaGetLastError();
+  }
   if (ce == cudaSuccess) ce = m->L.trace64(ma, m->ops64, m->d_Q0, T, st);
-  if (ce == cudaSuccess) ce = m->L.grad64(ma, m->ops64, ph, m->d_Q0, T, Tv, gr, nullptr, m->d_err, st);
+  if (ce == cudaSuccess) ce = m->L.grad64(ma, m->ops64, ph, m->d_Q0, T, Tv, gr, G, m->d_err, st);
   if (ce == cudaSuccess)
-    ce = m->L.resid64(ma, m->ops64, ph, m->d_Q0, T, Tv, nullptr, R0, nullptr, RkCoef<double>{}, 0.0, kModeResidual,
+    ce = m->L.resid64(ma, m->ops64, ph, m->d_Q0, T, Tv, G, R0, nullptr, RkCoef<double>{}, 0.0, kModeResidual,
                       m->d_err, st);
   if (ce == cudaSuccess) {
     k_d2f<<<grid1(5 * nP), 256, 0, st>>>((int64_t)(5 * nP), R0, m->d_R0);
@@ -549,13 +596,100 @@ chorus_status chorus_prepare(chorus_mesh m, const chorus_params* P, void* stream
     ce = cudaGetLastError();
   }
   if (ce == cudaSuccess) ce = cudaStreamSynchronize(st);
-  dev_free(T); dev_free(Tv); dev_free(R0); dev_free(gr);
+  dev_free(T); dev_free(Tv); dev_free(R0); dev_free(gr); dev_free(tab); dev_free(G);
   if (ce != cudaSuccess) {
     free_background(m);
     return CHORUS_ECUDA;
   }
   m->prep = *P;
   m->prepared = true;
+  return CHORUS_OK;
+}
+
+// Right-hand side of the almost-flux-balance equations (Section 4.3) for y = (rho_0, p_0).
+struct AfbRhs {
+  PhysArg<double> ph;
+  double Tc, Cp, L, kappa, kappa_r, gamma, GM;
+  void operator()(double r, const double y[2], double dy[2]) const {
+    const double chi = ph.chi_c + ph.chi_ad / r;
+    const double rho_a = ph.rho_c * std::pow(chi, ph.poly_n);
+    const double T_a = Tc * chi, dT_a = -Tc * ph.chi_ad / (r * r);
+    // the thermal balance integrated once with outward luminosity L (superadiabatic: Gamma < 0)
+    const double Gamma = -(L / (4.0 * kPi * r * r) + rho_a * Cp * kappa_r * dT_a) / (rho_a * T_a * kappa);
+    const double g = GM / (r * r);
+    dy[0] = -y[0] * (Gamma / Cp + g * y[0] / (gamma * y[1]));
+    dy[1] = -y[0] * g;
+  }
+  static constexpr double kPi = 3.14159265358979323846;
+};
+
+// classical fourth-order Runge-Kutta step of size h
+void rk4(const AfbRhs& f, double r, double h, double y[2]) {
+  double k1[2], k2[2], k3[2], k4[2], t[2];
+  f(r, y, k1);
+  for (int i = 0; i < 2; ++i) t[i] = y[i] + 0.5 * h * k1[i];
+  f(r + 0.5 * h, t, k2);
+  for (int i = 0; i < 2; ++i) t[i] = y[i] + 0.5 * h * k2[i];
+  f(r + 0.5 * h, t, k3);
+  for (int i = 0; i < 2; ++i) t[i] = y[i] + h * k3[i];
+  f(r + h, t, k4);
+  for (int i = 0; i < 2; ++i) y[i] += h / 6.0 * (k1[i] + 2.0 * k2[i] + 2.0 * k3[i] + k4[i]);
+}
+
+}  // namespace
+
+extern "C" {
+
+chorus_status chorus_prepare(chorus_mesh m, const chorus_params* P, void* stream) {
+  if (!m || !params_ok(P)) return CHORUS_EINVAL;
+  if (m->prepared && same_params(m->prep, *P)) return CHORUS_OK;  // keeps a tabulated background too
+  return prepare_background(m, P, 0, 0.0, 0.0, nullptr, nullptr, (cudaStream_t)stream);
+}
+
+chorus_status chorus_prepare_profile(chorus_mesh m, const chorus_params* P, int64_t n, double r0, double r1,
+                                     const double* rho0, const double* p0, void* stream) {
+  if (!m || !params_ok(P) || n < 4 || !rho0 || !p0 || !(r0 > 0.0) || !(r1 > r0)) return CHORUS_EINVAL;
+  for (int64_t j = 0; j < n; ++j)
+    if (!(rho0[j] > 0.0) || !(p0[j] > 0.0) || !std::isfinite(rho0[j]) || !std::isfinite(p0[j])) return CHORUS_EINVAL;
+  return prepare_background(m, P, n, r0, r1, rho0, p0, (cudaStream_t)stream);
+}
+
+chorus_status chorus_afb_profile(const chorus_params* P, double r_inner, double r_outer, double r0, double r1,
+                                 int64_t n, double* rho0, double* p0) {
+  if (!params_ok(P) || !(P->kappa > 0.0) || !(r_inner > 0.0) || !(r_outer > r_inner) || !(r0 > 0.0) || !(r1 > r0) ||
+      n < 2 || !rho0 || !p0)
+    return CHORUS_EINVAL;
+  AfbRhs f;
+  f.ph = phys_arg<double>(*P, r_inner, r_outer);
+  f.Tc = f.ph.p_c / (P->R_gas * f.ph.rho_c);
+  f.Cp = P->gamma * P->R_gas / (P->gamma - 1.0);
+  f.L = 4.0 * AfbRhs::kPi * r_inner * r_inner * P->bottom_flux;
+  f.kappa = P->kappa;
+  f.kappa_r = P->kappa_r;
+  f.gamma = P->gamma;
+  f.GM = P->GM;
+  // grid r_j = r0 + j h; integrate from the middle radius r_m of the shell through the grid points on
+  // each side of it in order, with kSub RK4 substeps per grid interval (partial first interval)
+  const double h = (r1 - r0) / (double)(n - 1);
+  const double rm = 0.5 * (r_inner + r_outer);
+  const double chi = f.ph.chi_c + f.ph.chi_ad / rm;
+  constexpr int kSub = 16;
+  int64_t first_up = 0;  // first grid point with r_j >= r_m
+  while (first_up < n && r0 + (double)first_up * h < rm) ++first_up;
+  for (int dir = -1; dir <= 1; dir += 2) {
+    double y[2] = {f.ph.rho_c * std::pow(chi, f.ph.poly_n), f.ph.p_c * std::pow(chi, f.ph.poly_n + 1.0)};
+    double r = rm;
+    for (int64_t j = dir > 0 ? first_up : first_up - 1; dir > 0 ? j < n : j >= 0; j += dir) {
+      const double rj = r0 + (double)j * h;
+      const double span = rj - r;
+      const int sub = (int)std::ceil(std::fabs(span) / h * kSub - 1e-9);
+      for (int s = 0; s < sub; ++s) rk4(f, r + span * s / sub, span / sub, y);
+      r = rj;
+      if (!(y[0] > 0.0) || !(y[1] > 0.0) || !std::isfinite(y[0]) || !std::isfinite(y[1])) return CHORUS_ENAN;
+      rho0[j] = y[0];
+      p0[j] = y[1];
+    }
+  }
   return CHORUS_OK;
 }
 
@@ -586,7 +720,7 @@ chorus_status chorus_residual(chorus_mesh m, const chorus_params* P, chorus_prec
     }));
     RkCoef<double> rc{};
     if (m->closure) {
-      CHK(mlp_elements(0, m->closure, Q, m->d_Q0, m->closure_buf, m->E, 0, st));
+      CHK(mlp_elements_tc(0, m->closure, Q, m->d_Q0, m->closure_buf, m->E, 0, m->d_err, st));
       rc.radd = (const double*)m->closure_buf;
     }
     CHK(timed(m, 2, st, [&] {
@@ -605,7 +739,7 @@ chorus_status chorus_residual(chorus_mesh m, const chorus_params* P, chorus_prec
   CHK(timed(m, 1, st, [&] { return m->L.grad32(ma, m->ops32, ph, bg, (const float*)Q, w.Ta, w.Tv, w.G, m->d_err, st); }));
   RkCoef<float> rc{};
   if (m->closure) {
-    CHK(mlp_elements(1, m->closure, Q, nullptr, m->closure_buf, m->E, 0, st));
+    CHK(mlp_elements_tc(1, m->closure, Q, nullptr, m->closure_buf, m->E, 0, m->d_err, st));
     rc.radd = (const float*)m->closure_buf;
   }
   CHK(timed(m, 2, st, [&] {
@@ -659,8 +793,8 @@ chorus_status run_rk(chorus_mesh_s* m, R* u, const Ws<R>& w, double dt, int64_t 
       RkCoef<R> c{buf[g.un], (R)g.a, (R)g.b, (R)g.c, g.un2 >= 0 ? buf[g.un2] : nullptr,
                   g.out2 >= 0 ? buf[g.out2] : nullptr, (R)g.a2, (R)g.b2, (R)g.c2, nullptr};
       if (m->closure) {
-        CHK(mlp_elements(sizeof(R) == 8 ? 0 : 1, m->closure, buf[g.src], sizeof(R) == 8 ? m->d_Q0 : nullptr,
-                         m->closure_buf, m->E, 0, st));
+        CHK(mlp_elements_tc(sizeof(R) == 8 ? 0 : 1, m->closure, buf[g.src], sizeof(R) == 8 ? m->d_Q0 : nullptr,
+                            m->closure_buf, m->E, 0, m->d_err, st));
         c.radd = (const R*)m->closure_buf;
       }
       CHK(timed(m, 1, st, [&] { return grad(buf[g.src], Tc); }));
@@ -774,6 +908,21 @@ chorus_status chorus_am_correct(chorus_mesh m, const chorus_params* P, chorus_pr
 
 size_t chorus_closure_bytes(void) { return closure_record_bytes(); }
 
+chorus_status chorus_closure_set_scales(void* weights, const float* in_scale, const float* out_scale, void* stream) {
+  if (!weights || !in_scale || !out_scale) return CHORUS_EINVAL;
+  for (int v = 0; v < 5; ++v)
+    if (!(in_scale[v] > 0.f) || !(out_scale[v] > 0.f)) return CHORUS_EINVAL;
+  float s[10];
+  for (int v = 0; v < 5; ++v) {
+    s[v] = in_scale[v];
+    s[5 + v] = out_scale[v];
+  }
+  cudaStream_t st = (cudaStream_t)stream;
+  CHK(cudaMemcpyAsync((unsigned char*)weights + ClosureLayout::oin, s, sizeof(s), cudaMemcpyHostToDevice, st));
+  CHK(cudaStreamSynchronize(st));
+  return CHORUS_OK;
+}
+
 chorus_status chorus_closure_init(void* weights, uint64_t seed, const float* in_scale, const float* out_scale,
                                   void* stream) {
   if (!weights || !in_scale || !out_scale) return CHORUS_EINVAL;
@@ -805,6 +954,12 @@ chorus_status chorus_closure_forward(const void* weights, const float* X, float*
   if (!weights || !X || !Y || n < 0) return CHORUS_EINVAL;
   if (n == 0) return CHORUS_OK;
   return cu(mlp_forward(weights, X, Y, n, (cudaStream_t)stream));
+}
+
+chorus_status chorus_closure_forward_tc(const void* weights, const float* X, float* Y, int64_t n, void* stream) {
+  if (!weights || !X || !Y || n < 0) return CHORUS_EINVAL;
+  if (n == 0) return CHORUS_OK;
+  return cu(mlp_forward_tc(weights, X, Y, n, nullptr, (cudaStream_t)stream));
 }
 
 chorus_status chorus_closure_grad(const void* weights, const float* X, const float* Y, int64_t n, float* grad,
@@ -876,8 +1031,14 @@ chorus_status chorus_closure_apply(chorus_mesh coarse, chorus_precision prec, co
                                    void* R, void* stream) {
   if (!coarse || coarse->p != 2 || !weights || !Q || !R) return CHORUS_EINVAL;
   if (prec == CHORUS_FP64 && !coarse->prepared) return CHORUS_EINVAL;
-  return cu(mlp_elements(prec == CHORUS_FP64 ? 0 : 1, weights, Q, prec == CHORUS_FP64 ? coarse->d_Q0 : nullptr, R,
-                         coarse->E, 1, (cudaStream_t)stream));
+  return cu(mlp_elements_tc(prec == CHORUS_FP64 ? 0 : 1, weights, Q, prec == CHORUS_FP64 ? coarse->d_Q0 : nullptr,
+                            R, coarse->E, 1, coarse->d_err, (cudaStream_t)stream));
+}
+
+chorus_status chorus_set_well_balanced(chorus_mesh m, int enable) {
+  if (!m) return CHORUS_EINVAL;
+  m->well_balanced = enable != 0;
+  return CHORUS_OK;
 }
 
 chorus_status chorus_closure_attach(chorus_mesh coarse, const void* weights) {
@@ -971,8 +1132,9 @@ extern "C" chorus_status chorus_residual_noalloc(chorus_mesh m, const chorus_par
   if (prec != CHORUS_FP64 && prec != CHORUS_FP32_PERT) return CHORUS_EINVAL;
   const size_t N2 = (size_t)m->N * m->N, E = (size_t)m->E;
   const size_t word = prec == CHORUS_FP64 ? sizeof(double) : sizeof(float);
-  const size_t nT = E * 6 * 5 * N2, nTv = E * 6 * 4 * N2;
-  if ((nT + nTv) * word > kNoAllocScratchBytes) return CHORUS_EINVAL;  // mesh too large for the scratch
+  const size_t N3 = N2 * (size_t)m->N;
+  const size_t nT = E * 6 * 5 * N2, nTv = E * 6 * 4 * N2, nG = E * kG * N3;
+  if ((nT + nTv + nG) * word > kNoAllocScratchBytes) return CHORUS_EINVAL;  // mesh too large for the scratch
   if (prec == CHORUS_FP32_PERT && (!m->prepared || !same_params(m->prep, *P))) return CHORUS_EINVAL;
   void* scratch = nullptr;
   chorus_status s = noalloc_scratch(&scratch);
@@ -983,9 +1145,10 @@ extern "C" chorus_status chorus_residual_noalloc(chorus_mesh m, const chorus_par
     const MeshArg<double> ma = mesh_arg<double>(m);
     double* T = (double*)scratch;
     double* Tv = T + nT;
+    double* G = Tv + nTv;
     CHK(m->L.trace64(ma, m->ops64, (const double*)Q, T, st));
-    CHK(m->L.grad64(ma, m->ops64, ph, (const double*)Q, T, Tv, nullptr, nullptr, m->d_err, st));
-    CHK(m->L.resid64(ma, m->ops64, ph, (const double*)Q, T, Tv, nullptr, (double*)R, nullptr, RkCoef<double>{}, 0.0,
+    CHK(m->L.grad64(ma, m->ops64, ph, (const double*)Q, T, Tv, nullptr, G, m->d_err, st));
+    CHK(m->L.resid64(ma, m->ops64, ph, (const double*)Q, T, Tv, G, (double*)R, nullptr, RkCoef<double>{}, 0.0,
                      kModeResidual, m->d_err, st));
     return CHORUS_OK;
   }
@@ -994,9 +1157,10 @@ extern "C" chorus_status chorus_residual_noalloc(chorus_mesh m, const chorus_par
   const BgArg bg = bg_arg(m);
   float* T = (float*)scratch;
   float* Tv = T + nT;
+  float* G = Tv + nTv;
   CHK(m->L.trace32(ma, m->ops32, (const float*)Q, T, st));
-  CHK(m->L.grad32(ma, m->ops32, ph, bg, (const float*)Q, T, Tv, nullptr, m->d_err, st));
-  CHK(m->L.resid32(ma, m->ops32, ph, bg, (const float*)Q, T, Tv, nullptr, (float*)R, nullptr, RkCoef<float>{}, 0.0f,
+  CHK(m->L.grad32(ma, m->ops32, ph, bg, (const float*)Q, T, Tv, G, m->d_err, st));
+  CHK(m->L.resid32(ma, m->ops32, ph, bg, (const float*)Q, T, Tv, G, (float*)R, nullptr, RkCoef<float>{}, 0.0f,
                    kModeResidual, m->d_err, st));
   return CHORUS_OK;
 }

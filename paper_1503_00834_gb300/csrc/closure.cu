@@ -248,38 +248,6 @@ __global__ void k_mlp_forward(const void* weights, const float* __restrict__ X, 
   for (int i = threadIdx.x; i < rows * NO; i += blockDim.x) Y[(r0 + i / NO) * NO + i % NO] = s.y[(i / NO) * SX + i % NO];
 }
 
-// Closure correction of element states: for element e the input is x[v*N3 + pt] = q'[e][v][pt] /
-// in_scale[v] (q' = Q - Q0 for total-state storage), the output C[e][v][pt] = out_scale[v] y[v*N3+pt].
-// accumulate = 1 adds C into `out`, 0 stores it.
-template <class R>
-__global__ void k_mlp_elements(const void* weights, const R* __restrict__ Q, const double* __restrict__ Q0,
-                               R* __restrict__ out, int64_t E, int accumulate) {
-  extern __shared__ __align__(16) unsigned char smraw[];
-  FwdSmem& s = *reinterpret_cast<FwdSmem*>(smraw);
-  const Rec w = rec_of(weights);
-  const int64_t e0 = (int64_t)blockIdx.x * TB;
-  const int rows = (int)((E - e0) < TB ? (E - e0) : TB);
-  constexpr int N3 = 27;
-  for (int i = threadIdx.x; i < TB * NI; i += blockDim.x) {
-    const int r = i / NI, k = i % NI, v = k / N3;
-    float x = 0.f;
-    if (r < rows) {
-      double q = (double)Q[(e0 + r) * NI + k];
-      if (Q0) q -= Q0[(e0 + r) * NI + k];
-      x = (float)(q / (double)w.in_scale[v]);
-    }
-    s.X[r * SX + k] = x;
-  }
-  __syncthreads();
-  forward_tile(w, s, rows);
-  for (int i = threadIdx.x; i < rows * NO; i += blockDim.x) {
-    const int r = i / NO, k = i % NO, v = k / N3;
-    const R c = (R)(s.y[r * SX + k] * w.out_scale[v]);
-    R* o = out + (e0 + r) * NO + k;
-    *o = accumulate ? *o + c : c;
-  }
-}
-
 // Training pairs: X = q'_c / in_scale, Y = (P R_f - R_c) / out_scale per element.
 template <class R>
 __global__ void k_make_pairs(const void* weights, const R* __restrict__ Qc, const double* __restrict__ Q0,
@@ -422,28 +390,10 @@ size_t mlp_smem_bytes(bool backward) {
   return sizeof(FwdSmem) + (backward ? sizeof(float) * TB * SH : 0);
 }
 
-template __global__ void k_mlp_elements<float>(const void*, const float*, const double*, float*, int64_t, int);
-template __global__ void k_mlp_elements<double>(const void*, const double*, const double*, double*, int64_t, int);
 template __global__ void k_make_pairs<float>(const void*, const float*, const double*, const float*, const float*,
                                              float*, float*, int64_t);
 template __global__ void k_make_pairs<double>(const void*, const double*, const double*, const double*,
                                               const double*, float*, float*, int64_t);
-
-cudaError_t mlp_elements(int prec, const void* weights, const void* Q, const double* Q0, void* out, int64_t E,
-                         int accumulate, cudaStream_t st) {
-  const size_t sm = mlp_smem_bytes(false);
-  const unsigned nb = (unsigned)((E + TB - 1) / TB);
-  if (prec == 0) {
-    cudaError_t e = cudaFuncSetAttribute(k_mlp_elements<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-    if (e != cudaSuccess) return e;
-    k_mlp_elements<double><<<nb, kThreads, sm, st>>>(weights, (const double*)Q, Q0, (double*)out, E, accumulate);
-  } else {
-    cudaError_t e = cudaFuncSetAttribute(k_mlp_elements<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-    if (e != cudaSuccess) return e;
-    k_mlp_elements<float><<<nb, kThreads, sm, st>>>(weights, (const float*)Q, Q0, (float*)out, E, accumulate);
-  }
-  return cudaGetLastError();
-}
 
 cudaError_t mlp_forward(const void* weights, const float* X, float* Y, int64_t n, cudaStream_t st) {
   const size_t sm = mlp_smem_bytes(false);

@@ -49,9 +49,12 @@ std::vector<unsigned char> init_record(uint64_t seed, const float* in_scale, con
 
 cudaError_t launch_project(int64_t E, int Nf, int Nc, int prec, const void* Qf, void* Qc, const double* add_f,
                            const double* sub_c, int nvar, cudaStream_t st);
-cudaError_t mlp_elements(int prec, const void* weights, const void* Q, const double* Q0, void* out, int64_t E,
-                         int accumulate, cudaStream_t st);
 cudaError_t mlp_forward(const void* weights, const float* X, float* Y, int64_t n, cudaStream_t st);
+// tensor-core forward (closure_tc.cu): BF16 layer inputs, FP32 accumulation; err (device) receives
+// bit 2 if a bounded wait ran out (may be null)
+cudaError_t mlp_elements_tc(int prec, const void* weights, const void* Q, const double* Q0, void* out, int64_t E,
+                            int accumulate, unsigned* err, cudaStream_t st);
+cudaError_t mlp_forward_tc(const void* weights, const float* X, float* Y, int64_t n, unsigned* err, cudaStream_t st);
 cudaError_t mlp_backward(const void* weights, const float* X, const float* T, int64_t n, int64_t row0, int64_t rows,
                          float* grad, double* loss, cudaStream_t st);
 cudaError_t make_pairs(int prec, const void* weights, const void* Qc, const double* Q0, const void* PRf,

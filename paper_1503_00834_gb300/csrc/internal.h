@@ -6,6 +6,8 @@
 namespace chorus {
 
 constexpr int kMaxN = 6;
+// entries of the gradient record per solution point: grad rho (3), trace-free strain (6), grad p (3)
+constexpr int kG = 12;
 
 // 1D operators for one order, passed to kernels by value (parameter bank).
 template <class R>
@@ -44,7 +46,7 @@ struct BgArg {
   const float* bg;     // [E][2][N^3]     rho0, E0
   const float* grho0;  // [E][3][N^3]     lifted background density gradient
   const float* bgT;    // [E][6][2][N^2]  rho0, E0 on the face points
-  const float* R0;     // [E][5][N^3]     FP64 residual of the background, rounded
+  const float* R0;     // [E][5][N^3]     FP64 residual of the background, rounded (null: left out)
 };
 
 enum ResidMode { kModeResidual = 0, kModeRK = 1 };
@@ -66,8 +68,8 @@ struct RkCoef {
 // Per-order launchers (defined in kern_p<N>.cu).  All return cudaGetLastError().
 struct LaunchSet {
   cudaError_t (*trace64)(const MeshArg<double>&, const OpsArg<double>&, const double* q, double* T, cudaStream_t);
-  // G: gradient record [E][12][N^3] written by grad (when non-null) and read by resid (when
-  // non-null, resid then skips the lifting)
+  // G: gradient record [E][12][N^3] written by grad (when non-null) and read by resid (required:
+  // resid returns cudaErrorInvalidValue without it)
   cudaError_t (*grad64)(const MeshArg<double>&, const OpsArg<double>&, const PhysArg<double>&, const double* q,
                         const double* T, double* Tv, double* grad_rho_out, double* G, unsigned* err, cudaStream_t);
   cudaError_t (*resid64)(const MeshArg<double>&, const OpsArg<double>&, const PhysArg<double>&, const double* q,

@@ -50,6 +50,8 @@ struct chorus_mesh_s {
   std::vector<Rec> recs;
   std::vector<cudaEvent_t> pool;
   // attached learned closure (p = 2 meshes): record pointer and its per-stage output buffer
+  // well-balanced perturbation residual: R(Q0) is left out, so the discrete background is steady
+  bool well_balanced = false;
   const void* closure = nullptr;
   void* closure_buf = nullptr;
 };

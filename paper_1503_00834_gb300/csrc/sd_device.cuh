@@ -127,7 +127,6 @@ __device__ __forceinline__ void flux_inv(const R q[5], const Pt<R>& st, const R 
 // Gradient record of a point, 12 entries: g[0..2] the form's grad rho, g[3..8] the trace-free
 // strain sigma = grad u + grad u^T - 2/3 (div u) I as (xx, yy, zz, xy, yz, zx), g[9..11] the form's
 // grad p.  tau = mu sigma (Eq. 9).
-constexpr int kG = 12;
 
 template <class R>
 __device__ __forceinline__ R sig(const R g[kG], int a, int b) {

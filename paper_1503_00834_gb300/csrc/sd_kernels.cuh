@@ -62,13 +62,22 @@ __device__ __forceinline__ int line_sidx(int ln, int s) {
   return sidx<N, R>(i, j, k);
 }
 
-template <int N, bool PERT, class R, int EPB>
+// Residual-kernel options (FP32 perturbation form): whether the background line data are staged in
+// shared memory (else read through L1 per flux point), and the resident CTAs per SM asked of the
+// compiler (register cap).
+constexpr bool kResidBgShared = true;
+constexpr int kResidMinBlocksF32 = 3;
+
+// RES: the residual kernel's layout (it reads the 12-entry gradient record instead of lifting, so the
+// gradient array holds kG components; the lifting kernel needs 15).
+template <int N, bool PERT, class R, int EPB, bool RES = false>
 struct Layout {
   static constexpr int N2 = N * N, N3 = N * N * N;
+  static constexpr bool bgShared = PERT && (!RES || kResidBgShared);
   static constexpr int SQ = pad_stride<R>(5 * N3);
-  static constexpr int SBG = PERT ? pad_stride<R>(2 * N3) : 0;
-  static constexpr int SGR0 = PERT ? pad_stride<R>(3 * N3) : 0;
-  static constexpr int SG = pad_stride<R>(15 * N3);
+  static constexpr int SBG = bgShared ? pad_stride<R>(2 * N3) : 0;
+  static constexpr int SGR0 = bgShared ? pad_stride<R>(3 * N3) : 0;
+  static constexpr int SG = pad_stride<R>((RES ? kG : 15) * N3);
   static constexpr int SDIV = pad_stride<R>(5 * N3);
   // interpolation I[f][s] and derivative D[i][f] tables, indexed at run time by rolled loops
   static constexpr int TAB = pad_stride<R>(2 * (N + 1) * N);
@@ -129,7 +138,7 @@ struct KArgs {
   R* Tv_out;           // grad kernel output
   R* grad_rho_out;     // optional grad kernel output: lifted d rho / d x_n [E][3][N3]
   R* G_out;            // optional grad kernel output: the gradient record [E][kG][N3] (shared layout)
-  const R* G_in;       // optional resid kernel input: that record (then the lifting is not redone)
+  const R* G_in;       // resid kernel input: that record
   R* out;              // residual or new state
   R* T_out;            // traces of the new state (RK mode)
   const R* un;         // first extra state of the RK combination
@@ -250,13 +259,13 @@ __global__ void __launch_bounds__(EPB * N * N) k_trace(const MeshArg<R> m, const
 
 // `between` runs after the copies are issued and before the wait (it issues the first sweep's
 // global loads so that both latencies overlap).
-template <int N, bool PERT, class R, int EPB, class Between>
+template <int N, bool PERT, class R, int EPB, bool RES, class Between>
 __device__ __forceinline__ void stage_elements(const KArgs<R>& A, R* sm, uint64_t* bar, int ne, Between&& between) {
-  using L = Layout<N, PERT, R, EPB>;
+  using L = Layout<N, PERT, R, EPB, RES>;
   constexpr int N3 = N * N * N;
   const int e0 = blockIdx.x * EPB;
   const bool tq = L::tmaQ && (((uintptr_t)A.q & 15u) == 0);
-  const bool tb = PERT && L::tmaBG && (((uintptr_t)A.bg.bg & 15u) == 0) && (((uintptr_t)A.bg.grho0 & 15u) == 0);
+  const bool tb = L::bgShared && L::tmaBG && (((uintptr_t)A.bg.bg & 15u) == 0) && (((uintptr_t)A.bg.grho0 & 15u) == 0);
   const bool tg = A.G_in != nullptr && ((kG * N3 * sizeof(R)) % 16 == 0) && (((uintptr_t)A.G_in & 15u) == 0);
   if (A.G_in != nullptr && !tg) {
     for (int i = threadIdx.x; i < ne * kG * N3; i += blockDim.x)
@@ -282,7 +291,7 @@ __device__ __forceinline__ void stage_elements(const KArgs<R>& A, R* sm, uint64_
     for (int i = threadIdx.x; i < ne * 5 * N3; i += blockDim.x)
       sm[L::oQ + (i / (5 * N3)) * L::SQ + i % (5 * N3)] = A.q[(size_t)e0 * 5 * N3 + i];
   }
-  if (PERT && !tb) {
+  if (L::bgShared && !tb) {
     for (int i = threadIdx.x; i < ne * 2 * N3; i += blockDim.x)
       sm[L::oBG + (i / (2 * N3)) * L::SBG + i % (2 * N3)] = (R)A.bg.bg[(size_t)e0 * 2 * N3 + i];
     for (int i = threadIdx.x; i < ne * 3 * N3; i += blockDim.x)
@@ -522,8 +531,9 @@ __device__ __forceinline__ void face_visc_dir(const KArgs<R>& A, const R* sm, in
   }
 }
 
+// FP32: four resident CTAs per SM (register cap 128; the shared memory of the lifting fits four)
 template <int N, bool PERT, class R, int EPB>
-__global__ void __launch_bounds__(EPB * N * N) k_grad(const KArgs<R> A) {
+__global__ void __launch_bounds__(EPB * N * N, sizeof(R) == 4 ? 4 : 1) k_grad(const KArgs<R> A) {
   constexpr int N2 = N * N;
   extern __shared__ __align__(128) unsigned char smem_raw[];
   __shared__ __align__(8) uint64_t bar;
@@ -537,7 +547,7 @@ __global__ void __launch_bounds__(EPB * N * N) k_grad(const KArgs<R> A) {
   fill_tables<N, R>(A.ops, sm + Layout<N, PERT, R, EPB>::oTAB);
   __syncthreads();
   LiftPre<N, R> pre;
-  stage_elements<N, PERT, R, EPB>(A, sm, &bar, ne, [&] {
+  stage_elements<N, PERT, R, EPB, false>(A, sm, &bar, ne, [&] {
     if (active) lift_prefetch<N, PERT, R, 0>(A, e, ln, pre);
   });
   __syncthreads();
@@ -572,7 +582,7 @@ __global__ void __launch_bounds__(EPB * N * N) k_grad(const KArgs<R> A) {
 // points (Eq. 18), accumulated into the divergence array.
 template <int N, bool PERT, class R, int EPB, int D>
 __device__ __forceinline__ void flux_dir(const KArgs<R>& A, R* sm, int el, int ln, int e, const FluxPre<R>& pre) {
-  using L = Layout<N, PERT, R, EPB>;
+  using L = Layout<N, PERT, R, EPB, true>;
   constexpr int N2 = N * N, N3 = N * N * N;
   const R* sq = sm + L::oQ + el * L::SQ;
   const R* sbg = sm + L::oBG + el * L::SBG;
@@ -648,10 +658,19 @@ __device__ __forceinline__ void flux_dir(const KArgs<R>& A, R* sm, int el, int l
 #pragma unroll
       for (int s = 0; s < N; ++s) {
         const int pt = line_pt<N, D>(ln, s);
-        P.r0 += w[s] * sbg[pt];
-        P.E0 += w[s] * sbg[N3 + pt];
+        if constexpr (L::bgShared) {
+          P.r0 += w[s] * sbg[pt];
+          P.E0 += w[s] * sbg[N3 + pt];
 #pragma unroll
-        for (int n = 0; n < 3; ++n) P.gr0[n] += w[s] * sgr0[n * N3 + pt];
+          for (int n = 0; n < 3; ++n) P.gr0[n] += w[s] * sgr0[n * N3 + pt];
+        } else {
+          const float* bge = A.bg.bg + (size_t)e * 2 * N3;
+          const float* gre = A.bg.grho0 + (size_t)e * 3 * N3;
+          P.r0 += w[s] * (R)__ldg(bge + pt);
+          P.E0 += w[s] * (R)__ldg(bge + N3 + pt);
+#pragma unroll
+          for (int n = 0; n < 3; ++n) P.gr0[n] += w[s] * (R)__ldg(gre + n * N3 + pt);
+        }
       }
     }
     const Pt<R> st = point_state<PERT>(P.q, P.r0, P.E0, ph);
@@ -729,8 +748,8 @@ __device__ __forceinline__ void flux_dir(const KArgs<R>& A, R* sm, int el, int l
 
 // FP32: ask for three resident CTAs per SM (register cap ~168 per thread)
 template <int N, bool PERT, class R, int EPB, int MODE>
-__global__ void __launch_bounds__(EPB * N * N, sizeof(R) == 4 ? 3 : 1) k_resid(const KArgs<R> A) {
-  using L = Layout<N, PERT, R, EPB>;
+__global__ void __launch_bounds__(EPB * N * N, sizeof(R) == 4 ? kResidMinBlocksF32 : 1) k_resid(const KArgs<R> A) {
+  using L = Layout<N, PERT, R, EPB, true>;
   constexpr int N2 = N * N, N3 = N * N * N;
   extern __shared__ __align__(128) unsigned char smem_raw[];
   __shared__ __align__(8) uint64_t bar;
@@ -741,21 +760,13 @@ __global__ void __launch_bounds__(EPB * N * N, sizeof(R) == 4 ? 3 : 1) k_resid(c
   const int e = e0 + el;
   const bool active = el < ne;
   if (threadIdx.x == 0) mbar_init(&bar);
-  fill_tables<N, R>(A.ops, sm + Layout<N, PERT, R, EPB>::oTAB);
+  fill_tables<N, R>(A.ops, sm + L::oTAB);
   __syncthreads();
-  const bool lift = A.G_in == nullptr;
   FluxPre<R> fp;
-  LiftPre<N, R> lp;
-  stage_elements<N, PERT, R, EPB>(A, sm, &bar, ne, [&] {
-    if (!active) return;
-    if (lift) lift_prefetch<N, PERT, R, 0>(A, e, ln, lp);
-    else flux_prefetch<N, PERT, R, 0>(A, e, ln, fp);
+  stage_elements<N, PERT, R, EPB, true>(A, sm, &bar, ne, [&] {
+    if (active) flux_prefetch<N, PERT, R, 0>(A, e, ln, fp);
   });
   __syncthreads();
-  if (lift) {
-    lift_all<N, PERT, R, EPB>(A, sm, el, ln, e, active, lp);
-    if (active) flux_prefetch<N, PERT, R, 0>(A, e, ln, fp);
-  }
   if (active) {
     flux_dir<N, PERT, R, EPB, 0>(A, sm, el, ln, e, fp);
     flux_prefetch<N, PERT, R, 1>(A, e, ln, fp);
@@ -782,7 +793,7 @@ __global__ void __launch_bounds__(EPB * N * N, sizeof(R) == 4 ? 3 : 1) k_resid(c
 #pragma unroll
       for (int v = 0; v < 5; ++v) {
         const size_t oi = ((size_t)e * 5 + v) * N3 + pt;
-        r0g[v][i] = PERT ? (R)__ldg(A.bg.R0 + oi) : R(0);
+        r0g[v][i] = (PERT && A.bg.R0) ? (R)__ldg(A.bg.R0 + oi) : R(0);
         ung[v][i] = (MODE == kModeRK) ? A.un[oi] : R(0);
       }
     }
@@ -876,7 +887,8 @@ struct Launch {
   template <int MODE>
   static cudaError_t resid(const KArgs<R>& A, cudaStream_t st) {
     if (A.m.E == 0) return cudaSuccess;
-    const size_t sm = (size_t)L::total_resid * sizeof(R);
+    if (A.G_in == nullptr) return cudaErrorInvalidValue;  // the residual kernel reads the gradient record
+    const size_t sm = (size_t)Layout<N, PERT, R, EPB, true>::total_resid * sizeof(R);
     cudaError_t e =
         cudaFuncSetAttribute(k_resid<N, PERT, R, EPB, MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
     if (e != cudaSuccess) return e;

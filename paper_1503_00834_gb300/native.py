@@ -27,10 +27,11 @@ EXPORTS = ("chorus_mesh_create", "chorus_mesh_destroy", "chorus_mesh_info", "cho
            "chorus_residual", "chorus_rk_workspace_bytes", "chorus_rk_step", "chorus_reduce", "chorus_check",
            "chorus_strerror", "chorus_timing_enable", "chorus_timing_read", "chorus_residual_noalloc",
            "chorus_am_correct", "chorus_rk_step_scheme", "chorus_closure_bytes", "chorus_closure_init",
-           "chorus_project", "chorus_closure_forward", "chorus_closure_grad", "chorus_closure_make_pairs",
-           "chorus_closure_train", "chorus_closure_apply", "chorus_closure_attach", "chorus_batch_create",
+           "chorus_project", "chorus_closure_forward", "chorus_closure_forward_tc", "chorus_closure_grad",
+           "chorus_closure_make_pairs", "chorus_closure_train", "chorus_closure_apply", "chorus_closure_attach", "chorus_batch_create",
            "chorus_batch_destroy", "chorus_batch_layout", "chorus_batch_init", "chorus_batch_rk_step",
-           "chorus_batch_reduce", "chorus_batch_autotune")
+           "chorus_batch_reduce", "chorus_batch_autotune", "chorus_set_well_balanced", "chorus_prepare_profile",
+           "chorus_afb_profile", "chorus_closure_set_scales")
 
 
 class ChorusError(RuntimeError):
@@ -98,13 +99,18 @@ def load() -> ctypes.CDLL:
         "chorus_rk_step_scheme": (i32, [vp, P(Params), i32, i32, vp, vp, f64, i64, vp]),
         "chorus_closure_bytes": (ctypes.c_size_t, []),
         "chorus_closure_init": (i32, [vp, ctypes.c_uint64, P(ctypes.c_float), P(ctypes.c_float), vp]),
+        "chorus_closure_set_scales": (i32, [vp, P(ctypes.c_float), P(ctypes.c_float), vp]),
         "chorus_project": (i32, [vp, vp, i32, i32, vp, vp, vp]),
         "chorus_closure_forward": (i32, [vp, vp, vp, i64, vp]),
+        "chorus_closure_forward_tc": (i32, [vp, vp, vp, i64, vp]),
         "chorus_closure_grad": (i32, [vp, vp, vp, i64, vp, P(f64), vp]),
         "chorus_closure_make_pairs": (i32, [vp, i32, vp, vp, vp, vp, vp, vp, vp]),
         "chorus_closure_train": (i32, [vp, vp, i64, vp, P(TrainCfg), P(f64), vp]),
         "chorus_closure_apply": (i32, [vp, i32, vp, vp, vp, vp]),
         "chorus_closure_attach": (i32, [vp, vp]),
+        "chorus_set_well_balanced": (i32, [vp, i32]),
+        "chorus_prepare_profile": (i32, [vp, P(Params), i64, f64, f64, P(f64), P(f64), vp]),
+        "chorus_afb_profile": (i32, [P(Params), f64, f64, f64, f64, i64, P(f64), P(f64)]),
         "chorus_batch_create": (i32, [i32, P(ShellDesc), f64, f64, P(Params), vp, P(vp)]),
         "chorus_batch_destroy": (i32, [vp]),
         "chorus_batch_layout": (i32, [vp, P(i64), P(i64), P(ctypes.c_size_t), P(i32), P(i32), P(f64)]),
@@ -181,6 +187,16 @@ class Mesh:
     def prepare(self, params: Params, stream=None) -> None:
         _ok("chorus_prepare", load().chorus_prepare(self.handle, ctypes.byref(params), _stream(stream)))
 
+    def prepare_profile(self, params: Params, profile, stream=None) -> None:
+        """Background from a radial profile (r0, r1, rho0, p0) on the uniform grid over [r0, r1]."""
+        r0, r1, rho0, p0 = profile
+        r = np.ascontiguousarray(rho0, dtype=np.float64)
+        p = np.ascontiguousarray(p0, dtype=np.float64)
+        dp = ctypes.POINTER(ctypes.c_double)
+        _ok("chorus_prepare_profile", load().chorus_prepare_profile(self.handle, ctypes.byref(params), r.shape[0], r0,
+                                                                    r1, r.ctypes.data_as(dp), p.ctypes.data_as(dp),
+                                                                    _stream(stream)))
+
     def workspace_bytes(self, prec: int) -> int:
         return int(load().chorus_rk_workspace_bytes(self.handle, prec))
 
@@ -224,6 +240,10 @@ class Mesh:
         cnt = (ctypes.c_int64 * 3)()
         _ok("chorus_timing_read", load().chorus_timing_read(self.handle, _stream(stream), ms, cnt))
         return list(ms), list(cnt)
+
+    def set_well_balanced(self, enable: bool) -> None:
+        """FP32 perturbation residual without R(Q0): the background becomes an exact steady state."""
+        _ok("chorus_set_well_balanced", load().chorus_set_well_balanced(self.handle, 1 if enable else 0))
 
     def check(self, stream=None) -> None:
         _ok("chorus_check", load().chorus_check(self.handle, _stream(stream)))
@@ -325,6 +345,12 @@ def closure_alloc(seed: int, in_scale, out_scale, stream=None):
     return w
 
 
+def closure_set_scales(w, in_scale, out_scale, stream=None) -> None:
+    a = (ctypes.c_float * 5)(*in_scale)
+    b = (ctypes.c_float * 5)(*out_scale)
+    _ok("chorus_closure_set_scales", load().chorus_closure_set_scales(_ptr(w), a, b, _stream(stream)))
+
+
 def project(fine: "Mesh", coarse: "Mesh", prec: int, kind: int, Qf, Qc, stream=None) -> None:
     _ok("chorus_project", load().chorus_project(fine.handle, coarse.handle, prec, kind, _ptr(Qf), _ptr(Qc),
                                                 _stream(stream)))
@@ -333,6 +359,12 @@ def project(fine: "Mesh", coarse: "Mesh", prec: int, kind: int, Qf, Qc, stream=N
 def closure_forward(w, X, Y, stream=None) -> None:
     _ok("chorus_closure_forward", load().chorus_closure_forward(_ptr(w), _ptr(X), _ptr(Y), X.shape[0],
                                                                 _stream(stream)))
+
+
+def closure_forward_tc(w, X, Y, stream=None) -> None:
+    """Tensor-core forward (BF16 layer inputs, FP32 accumulation)."""
+    _ok("chorus_closure_forward_tc", load().chorus_closure_forward_tc(_ptr(w), _ptr(X), _ptr(Y), X.shape[0],
+                                                                      _stream(stream)))
 
 
 def closure_grad(w, X, Y, grad, stream=None) -> float:
@@ -364,9 +396,26 @@ def closure_attach(coarse: "Mesh", w) -> None:
     _ok("chorus_closure_attach", load().chorus_closure_attach(coarse.handle, None if w is None else _ptr(w)))
 
 
+def afb_profile(params: Params, r_inner: float, r_outer: float, n: int = 16385, margin: float = 0.05):
+    """Almost-flux-balance profile (r0, r1, rho0, p0) on n uniform radii spanning the shell plus
+    `margin` of its thickness on both sides (host computation in the library)."""
+    d = r_outer - r_inner
+    r0, r1 = r_inner - margin * d, r_outer + margin * d
+    rho = np.empty(n)
+    p = np.empty(n)
+    dp = ctypes.POINTER(ctypes.c_double)
+    _ok("chorus_afb_profile", load().chorus_afb_profile(ctypes.byref(params), r_inner, r_outer, r0, r1, n,
+                                                        rho.ctypes.data_as(dp), p.ctypes.data_as(dp)))
+    return r0, r1, rho, p
+
+
 def stable_dt(p: int, h_min: float, wave_speed: float, diffusivity: float) -> float:
-    """Fixed explicit step: 0.5 h/((2p+1) max(|u|+c)), capped by 0.25 h^2/((2p+1)^2 max(nu, kappa))."""
-    dt = 0.5 * h_min / ((2 * p + 1) * wave_speed)
+    """Fixed explicit step: 0.25 h/((2p+1) max(|u|+c)), capped by 0.25 h^2/((2p+1)^2 max(nu, kappa)).
+
+    h/((2p+1) c) is the one-dimensional limit; an element with comparable edges shares it among
+    three directions, so the factor is 0.25 (below 1/3).  A factor 0.5 diverged within 18-30 steps
+    at p = 4 and 5 on near-isotropic elements."""
+    dt = 0.25 * h_min / ((2 * p + 1) * wave_speed)
     if diffusivity > 0:
         dt = min(dt, 0.25 * h_min * h_min / ((2 * p + 1) ** 2 * diffusivity))
     return dt

@@ -5,6 +5,7 @@
     BF16-rounded weights (FP32 accumulation on the GPU: 1e-5 relative forward, 1e-4 gradient);
   * training on pairs from a seeded p = 5 run reduces the loss, and the trained closure reduces the
     error of the p = 2 residual against the projected p = 5 residual on held-out snapshots;
+  * the tensor-core forward (BF16 layer inputs) against the oracle with the same roundings;
   * an attached closure enters chorus_residual exactly as chorus_closure_apply.
 """
 import numpy as np
@@ -131,6 +132,37 @@ def test_network_forward_and_gradient_match_oracle():
     assert np.linalg.norm(got - flat) < 1e-4 * np.linalg.norm(flat)
 
 
+def test_tensor_core_forward_matches_oracle():
+    """tcgen05 forward (BF16 layer inputs, FP32 accumulation) against the FP64 oracle with the same
+    BF16 roundings.  Remaining differences: FP32 accumulation of 144 products (~1e-6 relative) and
+    rare BF16 rounding ties decided differently by an FP32 and an FP64 activation; bound 1e-4."""
+    from oracle.closure import forward, forward_bf16_inputs
+    from paper_1503_00834_gb300 import native
+
+    w = native.closure_alloc(9, IN_SCALE, OUT_SCALE)
+    p = _oracle_params(w)
+    rng = np.random.default_rng(1)
+    for n in (1, 300, 4097):  # one sample, ragged tiles, many tiles per CTA
+        X = (2.0 * rng.standard_normal((n, 135))).astype(np.float32)
+        Xd = torch.tensor(X, device="cuda")
+        Yd = torch.empty_like(Xd)
+        native.closure_forward_tc(w, Xd, Yd)
+        Ys = torch.empty_like(Xd)
+        native.closure_forward(w, Xd, Ys)
+        torch.cuda.synchronize()
+        ref = forward_bf16_inputs(p, X.astype(np.float64))
+        got = Yd.cpu().numpy().astype(np.float64)
+        rel = np.linalg.norm(got - ref) / np.linalg.norm(ref)
+        ref32, _ = forward(p, X.astype(np.float64))
+        rel32 = np.linalg.norm(Ys.cpu().numpy() - ref32) / np.linalg.norm(ref32)
+        gap = np.linalg.norm(got - ref32) / np.linalg.norm(ref32)
+        print(f"n={n}: tensor-core vs BF16-input oracle {rel:.2e}; FP32 path vs oracle {rel32:.2e}; "
+              f"BF16-input gap {gap:.2e}")
+        assert rel < 1e-4
+        assert rel32 < 1e-5
+        assert gap < 1e-2
+
+
 def _collect(fine, coarse, w, n_snap, every, prec):
     from paper_1503_00834_gb300 import native
 
@@ -181,7 +213,7 @@ def test_training_reduces_loss_and_held_out_error():
 
 
 def test_attached_closure_enters_the_residual():
-    from oracle.closure import forward
+    from oracle.closure import forward_bf16_inputs
     from paper_1503_00834_gb300 import FP32_PERT, native
 
     _, coarse = _pair()
@@ -202,6 +234,12 @@ def test_attached_closure_enters_the_residual():
     # the correction itself against the oracle network
     C = (R1 - R0).double().cpu().numpy().reshape(-1, 135)
     X = (q.double().cpu().numpy().reshape(-1, 135) / 1e-3)
-    Yref, _ = forward(_oracle_params(w), X)
-    # C is a difference of two FP32 residuals, so compare to FP32 rounding of the residual size
-    assert np.allclose(C, Yref * 1e-2, rtol=1e-3, atol=1e-3 * np.abs(Yref * 1e-2).max())
+    Yref = forward_bf16_inputs(_oracle_params(w), X) * 1e-2
+    # C is a difference of two FP32 residuals (rounding 6e-8 |R|).  The network part: state inputs
+    # here reach |x| ~ 10 and more, where FP32 and FP64 pre-activations straddle BF16 rounding
+    # boundaries more often than in the unit-variance forward test; 1e-3 relative still sits a
+    # factor three below the whole BF16-input effect (~3e-3) and far below any wiring error.
+    err = np.linalg.norm(C - Yref)
+    bound = 1e-3 * np.linalg.norm(Yref) + 6e-8 * np.sqrt(C.size) * R1.abs().max().item()
+    print(f"attached closure: |C - oracle| = {err:.3e}, bound {bound:.3e}, max dev {np.abs(C - Yref).max():.3e}")
+    assert err <= bound

@@ -274,3 +274,50 @@ def test_freestream_on_gpu():
     k = np.arange(E) % cfg.n_r
     interior = (k >= 1) & (k < cfg.n_r - 1)
     assert np.abs(Rh[interior]).max() < 1e-13 * 1.3 * N * N / sh.h_min
+
+
+@pytest.mark.parametrize("n,n_r,p", [(8, 4, 5), (8, 2, 5), (16, 8, 4)])
+def test_time_step_rule_is_stable(n, n_r, p):
+    """Near-isotropic elements at p = 4, 5: 150 SSP-RK3 steps at the package's step stay finite
+    with bounded kinetic energy (with the factor 0.5 these shells went non-finite within 18-60
+    steps, in the oracle as in the library)."""
+    from paper_1503_00834_gb300 import FP32_PERT
+
+    cfg = small_shell(n, n_r, p)
+    sh = _gpu(cfg)
+    sh.mesh.prepare(sh.params)
+    Q = _alloc(sh.mesh, FP32_PERT)[0]
+    sh.mesh.state_init(sh.params, cfg.seed, cfg.entropy_amp, FP32_PERT, Q)
+    ws = _ws(sh.mesh, FP32_PERT)
+    sh.mesh.rk_step(sh.params, FP32_PERT, Q, ws, sh.dt, 10)
+    ke10 = sh.mesh.reduce(sh.params, FP32_PERT, Q)[2]
+    sh.mesh.rk_step(sh.params, FP32_PERT, Q, ws, sh.dt, 140)
+    ke150 = sh.mesh.reduce(sh.params, FP32_PERT, Q)[2]
+    print(f"{cfg.name}: KE {ke10:.3e} -> {ke150:.3e}")
+    assert np.isfinite(ke150) and ke150 <= 10.0 * ke10
+
+
+def test_well_balanced_residual_leaves_out_the_background_residual():
+    """With the option on, the residual of q' is R(Q0 + q') - R(Q0): zero for q' = 0 and the plain
+    residual minus the plain residual of the background otherwise, both to FP32 rounding."""
+    from paper_1503_00834_gb300 import FP32_PERT
+
+    cfg = small_shell(2, 2, 3)
+    sh = _gpu(cfg)
+    sh.mesh.prepare(sh.params)
+    q, zero, R, R0, Rw, Rw0 = _alloc(sh.mesh, FP32_PERT, 6)
+    ws = _ws(sh.mesh, FP32_PERT)
+    sh.mesh.state_init(sh.params, cfg.seed, 1e-2, FP32_PERT, q)
+    zero.zero_()
+    sh.mesh.residual(sh.params, FP32_PERT, q, R, ws)
+    sh.mesh.residual(sh.params, FP32_PERT, zero, R0, ws)
+    sh.mesh.set_well_balanced(True)
+    sh.mesh.residual(sh.params, FP32_PERT, q, Rw, ws)
+    sh.mesh.residual(sh.params, FP32_PERT, zero, Rw0, ws)
+    sh.mesh.set_well_balanced(False)
+    torch.cuda.synchronize()
+    # q' = 0: only FP32 rounding of the perturbation-form differences remains
+    assert R0.abs().max().item() > 0
+    assert Rw0.abs().max().item() <= 1e-6 * R0.abs().max().item(), (Rw0.abs().max().item(), R0.abs().max().item())
+    d = (Rw - (R - R0)).abs().max().item()
+    assert d <= 1e-5 * R.abs().max().item(), d

@@ -72,3 +72,31 @@ def test_adam_reduces_loss_on_a_fit():
         adam_step(p, g, st, 3e-3)
     l1, _ = loss_and_grad(p, X, T)
     assert l1 < 0.2 * l0
+
+
+def test_round_bf16_against_exact_values():
+    from oracle.closure import round_bf16
+
+    # exactly representable values stay; 1 + 2^-8 is a tie between 1 and 1 + 2^-7: even keeps 1;
+    # 1 + 3 * 2^-8 ties between 1 + 2^-7 (odd) and 1 + 2^-6 (even); above a tie rounds up
+    x = np.array([1.0, -2.5, 1.0 + 2.0 ** -8, 1.0 + 3 * 2.0 ** -8, 1.0 + 2.0 ** -8 + 2.0 ** -20, 3.0e-39, 0.0])
+    want = np.array([1.0, -2.5, 1.0, 1.0 + 2.0 ** -6, 1.0 + 2.0 ** -7, None, 0.0], dtype=object)
+    got = round_bf16(x)
+    for g, w in zip(got, want):
+        if w is not None:
+            assert g == w
+    # relative rounding error at most 2^-8 for normal numbers
+    rng = np.random.default_rng(3)
+    v = rng.standard_normal(10000) * 10.0 ** rng.uniform(-5, 5, 10000)
+    assert np.all(np.abs(round_bf16(v) - v.astype(np.float32)) <= 2.0 ** -8 * np.abs(v.astype(np.float32)))
+
+
+def test_forward_bf16_inputs_close_to_forward():
+    from oracle.closure import forward, forward_bf16_inputs, init_params
+
+    p = init_params(4)
+    X = np.random.default_rng(5).standard_normal((64, 135))
+    Y, _ = forward(p, X)
+    Yb = forward_bf16_inputs(p, X)
+    rel = np.linalg.norm(Yb - Y) / np.linalg.norm(Y)
+    assert 1e-5 < rel < 1e-2  # BF16 inputs perturb the result at the 2^-9 level, no more
