@@ -49,6 +49,22 @@ def _dist():
     return rank, world, local
 
 
+def max_over_ranks(ms: float, world: int, device: str = "cuda") -> float:
+    """The slowest rank's time (the job's time); a no-op for one rank."""
+    if world <= 1:
+        return ms
+    import torch
+
+    t = torch.tensor([ms], dtype=torch.float64, device=device)
+    torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_rate(world: int, units_per_rank: float, seconds: float) -> float:
+    """Whole-job throughput: every rank processes its own replica's units in the job's time."""
+    return world * units_per_rank / seconds
+
+
 def _peaks():
     path = os.path.join(ROOT, "MEASURED_PEAKS.json")
     try:
@@ -187,15 +203,11 @@ def run_batch(args, rank, world, local):
         torch.distributed.barrier()
     torch.cuda.synchronize()
     clocks = clk.stop()
-    ms = ev0.elapsed_time(ev1)
-    if world > 1:
-        t = torch.tensor([ms], device="cuda")
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        ms = float(t.item())
+    ms = max_over_ranks(ev0.elapsed_time(ev1), world)
     red = b.reduce(Q)  # also reports any device-side error flag
     n_dof = b.n_dof()
     stages = 3 * args.steps
-    value = world * n_dof * stages / (ms / 1e3)
+    value = job_rate(world, n_dof * stages, ms / 1e3)
     alg = sum(e * (p + 1) ** 3 * ALG_BYTES_PER_DOF_STAGE[p] for e, p in zip(b.n_elem, b.orders))
     peak, peak_kind = _peaks()
     achieved = alg / (ms / stages / 1e3) / 1e9
@@ -344,13 +356,9 @@ def main():
     clocks = clk.stop()
     kms, kcnt = mesh.timing_read()
     mesh.timing_enable(False)
-    ms = ev0.elapsed_time(ev1)
-    if world > 1:
-        t = torch.tensor([ms], device="cuda")
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        ms = float(t.item())
+    ms = max_over_ranks(ev0.elapsed_time(ev1), world)
     stages = 3 * args.steps
-    value = world * n_dof * stages / (ms / 1e3)
+    value = job_rate(world, n_dof * stages, ms / 1e3)
     mesh.check()
 
     # ---- dominant kernel roofline (residual + stage update kernel)

@@ -131,6 +131,8 @@ class PhysParams:
     rho_c: float
     bottom_flux: float
     T_top: float
+    kappa_r1: float = 0.0  # radiative diffusivity kappa_r(r) = kappa_r + kappa_r1 r + kappa_r2 r^2
+    kappa_r2: float = 0.0
 
     def as_tuple(self):
         return dataclasses.astuple(self)
@@ -272,15 +274,17 @@ PAPER_CASES = {
     # Table 1 (Jupiter benchmark): kappa_r = 0
     "jupiter": dict(beta=0.35, n=2.0, N_rho=5.0, R_o=7.0e9, Omega=1.76e-4, M=1.9e30, rho_i=1.1, nu=3.64364e12,
                     kappa=3.64364e12, L=7.014464e32),
-    # Table 2 (solar benchmark); its radiative diffusion profile kappa_r(r) is not modelled (kappa_r = 0)
+    # Table 2 (solar benchmark) with the radiative diffusivity of Section 7.2:
+    # kappa_r = lambda (c0 + c1 w + c2 w^2), w = r / 1e10 cm, lambda such that the radiative flux
+    # carries L at the bottom
     "sun": dict(beta=0.736762, n=1.5, N_rho=3.0, R_o=6.61e10, Omega=8.1e-5, M=1.98891e33, rho_i=0.21, nu=6.0e13,
-                kappa=6.0e13, L=3.846e36),
+                kappa=6.0e13, L=3.846e36, kappa_r_poly=(1.5600975e8, -4.5631718e7, 3.3370368e6)),
 }
 
 
 def paper_case_phys(name: str) -> tuple:
     """(beta, PhysParams) of a Table 1/2 case; bottom_flux = L / (4 pi r_i^2), T_top left NaN (the
-    caller sets it from the stratification it uses)."""
+    caller sets it from the stratification it uses); the solar case carries its kappa_r(r)."""
     c = PAPER_CASES[name]
     beta, n = c["beta"], c["n"]
     t_u = math.sqrt(c["R_o"] ** 3 / (_G_CGS * c["M"]))
@@ -290,7 +294,22 @@ def paper_case_phys(name: str) -> tuple:
     L = c["L"] * t_u ** 3 / (rho_c * c["R_o"] ** 5)
     nu = c["nu"] * t_u / c["R_o"] ** 2
     kappa = c["kappa"] * t_u / c["R_o"] ** 2
-    phys = PhysParams(gamma=1.0 + 1.0 / n, R_gas=1.0, GM=1.0, Omega=c["Omega"] * t_u, nu=nu, kappa=kappa, kappa_r=0.0,
+    gamma = 1.0 + 1.0 / n
+    kr = (0.0, 0.0, 0.0)
+    if "kappa_r_poly" in c:
+        # lambda from F_r = -kappa_r rho_a C_p dT_a/dr = L / (4 pi r_i^2) at r_i = beta, with the
+        # polytrope of Section 4.2 in these units (rho_c = 1, gas constant 1, GM = 1)
+        d = 1.0 - beta
+        alpha = (1.0 + beta) * (1.0 - chi_o) / d ** 2
+        T_c = 1.0 / ((n + 1.0) * alpha * d)
+        dTdr_i = -T_c * alpha * d / beta ** 2
+        Cp = gamma / (gamma - 1.0)
+        kr_i = L / (4.0 * math.pi * beta ** 2) / (chi_i ** n * Cp * -dTdr_i)
+        s = c["R_o"] * 1e-10  # w = s r
+        c0, c1, c2 = c["kappa_r_poly"]
+        lam = kr_i / (c0 + c1 * s * beta + c2 * (s * beta) ** 2)
+        kr = (lam * c0, lam * c1 * s, lam * c2 * s * s)
+    phys = PhysParams(gamma=gamma, R_gas=1.0, GM=1.0, Omega=c["Omega"] * t_u, nu=nu, kappa=kappa, kappa_r=kr[0],
                       poly_n=n, N_rho=c["N_rho"], rho_c=1.0, bottom_flux=L / (4.0 * math.pi * beta * beta),
-                      T_top=float("nan"))
+                      T_top=float("nan"), kappa_r1=kr[1], kappa_r2=kr[2])
     return beta, phys

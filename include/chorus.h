@@ -61,15 +61,20 @@ typedef enum { CHORUS_FP64 = 0, CHORUS_FP32_PERT = 1 } chorus_precision;
 /* Physical parameters (paper Section 2, Eq. 24, Section 4.2, Section 5), nondimensional.
  * gamma, R_gas: ideal gas (Eq. 22); GM: gravity g = GM/r^2; Omega: rotation about +z;
  * nu: kinematic viscosity (mu = rho nu, Eq. 9); kappa: entropy diffusivity; kappa_r: thermal
- * diffusivity (f = -kappa rho T grad S - kappa_r rho C_p grad T); poly_n, N_rho, rho_c:
+ * (radiative) diffusivity (f = -kappa rho T grad S - kappa_r rho C_p grad T); poly_n, N_rho, rho_c:
  * polytrope of Eqs. 25-27 (beta = r_inner / r_outer from the mesh); bottom_flux: f.r_hat
  * imposed on the inner wall (L / (4 pi R_i^2)); T_top: temperature imposed on the outer wall,
- * NaN meaning the polytrope temperature at r_outer. */
+ * NaN meaning the polytrope temperature at r_outer; kappa_r1, kappa_r2: a radial profile of the
+ * radiative diffusivity, kappa_r(r) = kappa_r + kappa_r1 r + kappa_r2 r^2 (the solar benchmark's
+ * quadratic, Section 7.2); 0, 0 for a constant.  A varying profile enters the fluxes as its values
+ * at the solution points interpolated to the flux points (Eq. 17), like the solution itself, and
+ * must be non-negative at both walls (else CHORUS_EINVAL). */
 typedef struct {
   double gamma, R_gas, GM, Omega;
   double nu, kappa, kappa_r;
   double poly_n, N_rho, rho_c;
   double bottom_flux, T_top;
+  double kappa_r1, kappa_r2;
 } chorus_params;
 
 /* Build a mesh handle from 20-node hexahedra (Section 3 iso-parametric map, Section 5 20-node
@@ -109,7 +114,7 @@ chorus_status chorus_prepare_profile(chorus_mesh mesh, const chorus_params* para
                                      const double* rho0, const double* p0, void* stream);
 
 /* The almost-flux-balance stratification of Section 4.3 on the uniform grid above (host; no GPU):
- * target entropy gradient Gamma(r) = -(L/(4 pi r^2) + rho_a C_p kappa_r dT_a/dr) / (rho_a T_a kappa)
+ * target entropy gradient Gamma(r) = -(L/(4 pi r^2) + rho_a C_p kappa_r(r) dT_a/dr) / (rho_a T_a kappa)
  * (the thermal balance of Section 4.1 integrated with outward luminosity L; superadiabatic)
  * with L = 4 pi r_inner^2 bottom_flux and the polytrope rho_a, T_a of params and the shell radii,
  * then drho0/dr = -rho0 (Gamma/C_p + g rho0/(gamma p0)), dp0/dr = -rho0 g (g = GM/r^2), integrated

@@ -5,7 +5,7 @@ Test infrastructure only (see the package docstring).
 Steps, in the paper's order:
   1. the polytropic adiabatic reference rho_a, p_a, T_a (Section 4.2, Physics.polytrope);
   2. the target entropy gradient of Section 4.3,
-         Gamma(r) = -(L / (4 pi r^2) + rho_a C_p kappa_r dT_a/dr) / (rho_a T_a kappa),
+         Gamma(r) = -(L / (4 pi r^2) + rho_a C_p kappa_r(r) dT_a/dr) / (rho_a T_a kappa),
      with the luminosity L = 4 pi r_i^2 f_b from the imposed bottom flux f_b (Section 5).
      Reading: the printed Gamma has no leading minus, but it is the thermal-balance equation of
      Section 4.1 integrated once with an outward luminosity L (total flux
@@ -44,7 +44,7 @@ def dT_a_dr(ph: Physics, r):
 
 def target_entropy_gradient(ph: Physics, r):
     """Gamma(r) of Section 4.3 (with the sign of the reading above)."""
-    return -(luminosity(ph) / (4.0 * math.pi * r ** 2) + ph.rho_a(r) * ph.Cp * ph.kappa_r * dT_a_dr(ph, r)) / (
+    return -(luminosity(ph) / (4.0 * math.pi * r ** 2) + ph.rho_a(r) * ph.Cp * ph.kappa_r_at(r) * dT_a_dr(ph, r)) / (
         ph.rho_a(r) * ph.T_a(r) * ph.kappa)
 
 

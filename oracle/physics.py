@@ -38,12 +38,23 @@ class Physics:
     rho_c: float
     bottom_flux: float
     T_top: float
+    kappa_r1: float
+    kappa_r2: float
     r_inner: float
     r_outer: float
 
     @classmethod
     def from_params(cls, phys, r_inner: float, r_outer: float) -> "Physics":
         return cls(*phys.as_tuple(), r_inner, r_outer)
+
+    @property
+    def kappa_r_varies(self) -> bool:
+        return self.kappa_r1 != 0.0 or self.kappa_r2 != 0.0
+
+    def kappa_r_at(self, r):
+        """Radiative diffusivity kappa_r(r) = kappa_r + kappa_r1 r + kappa_r2 r^2 (the solar
+        benchmark's quadratic profile, Section 7.2; constant when the last two vanish)."""
+        return self.kappa_r + self.kappa_r1 * r + self.kappa_r2 * r * r
 
     @property
     def Cp(self) -> float:
@@ -141,19 +152,22 @@ def stress(Q: np.ndarray, gradW: np.ndarray, ph: Physics) -> np.ndarray:
     return tau
 
 
-def heat_flux(rho, p, grad_rho, grad_p, ph: Physics) -> np.ndarray:
-    """f = -kappa rho T grad S - kappa_r rho C_p grad T (Section 2), written in rho, p."""
+def heat_flux(rho, p, grad_rho, grad_p, ph: Physics, kr=None) -> np.ndarray:
+    """f = -kappa rho T grad S - kappa_r rho C_p grad T (Section 2), written in rho, p.
+    kr: the radiative diffusivity at the points (default: the constant ph.kappa_r)."""
     pr = (p / rho)[..., None]
     rhoT_gradS = (ph.Cp / ph.R_gas) * (grad_p / ph.gamma - pr * grad_rho)
     rhoCp_gradT = (ph.Cp / ph.R_gas) * (grad_p - pr * grad_rho)
-    return -ph.kappa * rhoT_gradS - ph.kappa_r * rhoCp_gradT
+    kr = ph.kappa_r if kr is None else np.asarray(kr)[..., None]
+    return -ph.kappa * rhoT_gradS - kr * rhoCp_gradT
 
 
-def viscous_flux(Q: np.ndarray, gradW: np.ndarray, ph: Physics) -> np.ndarray:
-    """Eqs. 7-8 (energy entry signed per Eq. 3): F_v -> [..., 3(n), 5]."""
+def viscous_flux(Q: np.ndarray, gradW: np.ndarray, ph: Physics, kr=None) -> np.ndarray:
+    """Eqs. 7-8 (energy entry signed per Eq. 3): F_v -> [..., 3(n), 5].  kr: radiative diffusivity at
+    the points (default the constant)."""
     rho, u, p = primitives(Q, ph)
     tau = stress(Q, gradW, ph)
-    f = heat_flux(rho, p, gradW[..., 0, :], gradW[..., 4, :], ph)
+    f = heat_flux(rho, p, gradW[..., 0, :], gradW[..., 4, :], ph, kr)
     Fv = np.zeros(Q.shape[:-1] + (3, 5))
     for n in range(3):
         for a in range(3):

@@ -146,6 +146,13 @@ def residual(disc: Discretization, ph: Physics, Q: np.ndarray, elems=None) -> np
 
     # ---- step 2: lifted gradients for S1
     g1 = disc.geometry(S1)
+    # a radial radiative-diffusivity profile enters like the solution: its values at the solution
+    # points, interpolated to the flux points (Eq. 17); each face side uses its own interpolant
+    krf1 = krface = None
+    if ph.kappa_r_varies:
+        x1 = g1["x"]
+        krf1 = interp_to_flux(ops, ph.kappa_r_at(np.sqrt(x1[:, 0] ** 2 + x1[:, 1] ** 2 + x1[:, 2] ** 2)))
+        krface = np.stack([face_values(krf1, F) for F in range(6)], axis=1)  # [S1,6,N2]
     i1 = loc[S1]
     Qf1 = tuple(a[i1].copy() for a in Qf2)
     Qc_all = []
@@ -194,7 +201,8 @@ def residual(disc: Discretization, ph: Physics, Q: np.ndarray, elems=None) -> np
     for d in range(3):
         Qd = _last(Qf[d], 1)  # [..., 5]
         gd = np.moveaxis(gWf[d], (1, 2), (-2, -1))  # [..., 5, 3]
-        Ftot = inviscid_flux(Qd, ph) - viscous_flux(Qd, gd, ph)  # [..., 3(n), 5]
+        krd = None if krf1 is None else krf1[d][ie]
+        Ftot = inviscid_flux(Qd, ph) - viscous_flux(Qd, gd, ph, krd)  # [..., 3(n), 5]
         Sd = _last(g0["S"][d], 1)  # [..., 3(n)]
         Ftil.append(np.moveaxis(np.einsum("...n,...nv->...v", Sd, Ftot), -1, 1))  # [e,5,...]
 
@@ -205,6 +213,7 @@ def residual(disc: Discretization, ph: Physics, Q: np.ndarray, elems=None) -> np
         nhat = sigma * Sf / mag[..., None]
         q_own = _last(trace[loc[elems], F], 1)  # [e,N2,5]
         gw_own = np.moveaxis(gface[ie, F], -1, 1)  # [e,N2,5,3]
+        kr_own = None if krface is None else krface[ie, F]  # [e,N2]
         Fn = np.zeros_like(q_own)
         nb = conn.nbr[elems, F]
         inner = nb >= 0
@@ -214,8 +223,10 @@ def residual(disc: Discretization, ph: Physics, Q: np.ndarray, elems=None) -> np
             q_nb = trace[loc[nb[inner]][:, None], nf, :, pidx]  # [S,N2,5]
             gw_nb = gface[loc1[nb[inner]][:, None], nf, :, :, pidx]  # [S,N2,5,3]
             nh = nhat[inner]
-            Fv_own = np.einsum("...n,...nv->...v", nh, viscous_flux(q_own[inner], gw_own[inner], ph))
-            Fv_nb = np.einsum("...n,...nv->...v", nh, viscous_flux(q_nb, gw_nb, ph))
+            kr_i = None if kr_own is None else kr_own[inner]
+            kr_nb = None if krface is None else krface[loc1[nb[inner]][:, None], nf, pidx]  # [S,N2]
+            Fv_own = np.einsum("...n,...nv->...v", nh, viscous_flux(q_own[inner], gw_own[inner], ph, kr_i))
+            Fv_nb = np.einsum("...n,...nv->...v", nh, viscous_flux(q_nb, gw_nb, ph, kr_nb))
             Fn[inner] = rusanov(q_own[inner], q_nb, nh, ph) - 0.5 * (Fv_own + Fv_nb)
         wall = ~inner
         if np.any(wall):
@@ -227,7 +238,7 @@ def residual(disc: Discretization, ph: Physics, Q: np.ndarray, elems=None) -> np
             trac = np.einsum("...a,...ab,...b->...", nh, tau, nh)
             top = (conn.wall[elems[wall], F] == 2)[:, None]
             p_top = ph.R_gas * rho * ph.T_wall_top
-            f_top = heat_flux(rho, p_top, gwo[..., 0, :], gwo[..., 4, :], ph)
+            f_top = heat_flux(rho, p_top, gwo[..., 0, :], gwo[..., 4, :], ph, None if kr_own is None else kr_own[wall])
             fn = np.where(top, np.sum(f_top * nh, axis=-1), -ph.bottom_flux)
             Fw = np.zeros_like(qo)
             Fw[..., 1:4] = (p - trac)[..., None] * nh

@@ -33,11 +33,13 @@ template <class R>
 MeshArg<R> mesh_arg(const chorus_mesh_s* m);
 template <>
 MeshArg<double> mesh_arg<double>(const chorus_mesh_s* m) {
-  return MeshArg<double>{(int)m->E, m->d_nbr, m->d_code, m->d_Sf64, m->d_invJ64, m->d_x64};
+  return MeshArg<double>{(int)m->E, m->d_nbr,   m->d_code, m->d_Sf64,
+                         m->d_invJ64, m->d_x64, m->kr_active ? m->d_kr64 : nullptr};
 }
 template <>
 MeshArg<float> mesh_arg<float>(const chorus_mesh_s* m) {
-  return MeshArg<float>{(int)m->E, m->d_nbr, m->d_code, m->d_Sf32, m->d_invJ32, m->d_x32};
+  return MeshArg<float>{(int)m->E, m->d_nbr,   m->d_code, m->d_Sf32,
+                        m->d_invJ32, m->d_x32, m->kr_active ? m->d_kr32 : nullptr};
 }
 
 template <class R>
@@ -72,7 +74,9 @@ PhysArg<R> phys_arg(const chorus_params& P, double r_inner, double r_outer) {
 }
 
 bool params_ok(const chorus_params* P) {
-  return P && P->gamma > 1.0 && P->R_gas > 0 && P->GM > 0 && P->nu >= 0 && P->kappa >= 0 && P->kappa_r >= 0 &&
+  return P && P->gamma > 1.0 && P->R_gas > 0 && P->GM > 0 && P->nu >= 0 && P->kappa >= 0 &&
+         (P->kappa_r >= 0 || P->kappa_r1 != 0.0 || P->kappa_r2 != 0.0) && std::isfinite(P->kappa_r1) &&
+         std::isfinite(P->kappa_r2) &&
          P->poly_n > 0 && P->N_rho > 0 && P->rho_c > 0 && std::isfinite(P->Omega) && std::isfinite(P->bottom_flux);
 }
 
@@ -131,6 +135,28 @@ __global__ void k_background_table(int64_t n_pts, int N3, const double* __restri
   Qe[2 * N3 + pt] = 0.0;
   Qe[3 * N3 + pt] = 0.0;
   Qe[4 * N3 + pt] = p / gm1;
+}
+
+// radiative diffusivity kappa_r(r) = a0 + a1 r + a2 r^2 at the flux points, as the interpolant (Eq. 17)
+// of its solution-point values along each line; layout [E][3 d][N+1 f][N*N line] like the metrics
+__global__ void k_kr_table(int64_t E, int N, const double* __restrict__ x, OpsArg<double> ops, double a0, double a1,
+                           double a2, double* __restrict__ kr64, float* __restrict__ kr32) {
+  const int N2 = N * N, N3 = N2 * N, per = 3 * (N + 1) * N2;
+  const int64_t g = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (g >= E * per) return;
+  const int64_t e = g / per;
+  const int rem = (int)(g % per), D = rem / ((N + 1) * N2), f = (rem % ((N + 1) * N2)) / N2, ln = rem % N2;
+  const int a = ln % N, b = ln / N;
+  double v = 0.0;
+  for (int s = 0; s < N; ++s) {
+    const int i = D == 0 ? s : a, j = D == 0 ? a : (D == 1 ? s : b), k = D == 2 ? s : b;
+    const int pt = i + N * j + N2 * k;
+    const double x0 = x[(e * 3 + 0) * N3 + pt], x1 = x[(e * 3 + 1) * N3 + pt], x2 = x[(e * 3 + 2) * N3 + pt];
+    const double r = sqrt(x0 * x0 + x1 * x1 + x2 * x2);
+    v += ops.I[f][s] * (a0 + (a1 + a2 * r) * r);
+  }
+  kr64[g] = v;
+  kr32[g] = (float)v;
 }
 
 __device__ __forceinline__ uint64_t splitmix64(uint64_t x) {
@@ -366,6 +392,8 @@ void free_mesh(chorus_mesh_s* m) {
   dev_free(m->d_Sf32);
   dev_free(m->d_invJ32);
   dev_free(m->d_x32);
+  dev_free(m->d_kr64);
+  dev_free(m->d_kr32);
   dev_free(m->d_err);
   dev_free(m->d_red);
   delete m;
@@ -419,6 +447,30 @@ bool same_params(const chorus_params& a, const chorus_params& b) {
 }
 
 inline dim3 grid1(int64_t n, int bs = 256) { return dim3((unsigned)((n + bs - 1) / bs)); }
+
+// Build (or refresh) the radiative-diffusivity table when the params vary kappa_r with radius.
+chorus_status ensure_kr(chorus_mesh_s* m, const chorus_params& P, cudaStream_t st) {
+  const bool active = P.kappa_r1 != 0.0 || P.kappa_r2 != 0.0;
+  if (!active) {
+    m->kr_active = false;
+    return CHORUS_OK;
+  }
+  auto kr_at = [&](double r) { return P.kappa_r + (P.kappa_r1 + P.kappa_r2 * r) * r; };
+  if (!(kr_at(m->r_inner) >= 0.0) || !(kr_at(m->r_outer) >= 0.0)) return CHORUS_EINVAL;
+  if (m->kr_active && m->kr_coef[0] == P.kappa_r && m->kr_coef[1] == P.kappa_r1 && m->kr_coef[2] == P.kappa_r2)
+    return CHORUS_OK;
+  const int64_t nF = m->E * 3 * (m->N + 1) * m->N * m->N;
+  if (!m->d_kr64 && (dev_alloc(&m->d_kr64, (size_t)nF) != cudaSuccess || dev_alloc(&m->d_kr32, (size_t)nF) != cudaSuccess))
+    return CHORUS_ENOMEM;
+  k_kr_table<<<grid1(nF), 256, 0, st>>>(m->E, m->N, m->d_x64, m->ops64, P.kappa_r, P.kappa_r1, P.kappa_r2, m->d_kr64,
+                                        m->d_kr32);
+  if (cudaGetLastError() != cudaSuccess) return CHORUS_ECUDA;
+  m->kr_coef[0] = P.kappa_r;
+  m->kr_coef[1] = P.kappa_r1;
+  m->kr_coef[2] = P.kappa_r2;
+  m->kr_active = true;
+  return CHORUS_OK;
+}
 
 LaunchSet launchers_for(int p, int tile) {
   switch (p) {
@@ -553,6 +605,8 @@ namespace {
 // gradient and the FP32 tables of the perturbation form.
 chorus_status prepare_background(chorus_mesh_s* m, const chorus_params* P, int64_t n_tab, double r0, double r1,
                                  const double* rho_tab, const double* p_tab, cudaStream_t st) {
+  const chorus_status ks = ensure_kr(m, *P, st);
+  if (ks != CHORUS_OK) return ks;
   free_background(m);
   const int N = m->N, N2 = N * N, N3 = N2 * N;
   const size_t E = m->E, nP = E * N3, nT = E * 6 * 5 * N2;
@@ -609,13 +663,14 @@ chorus_status prepare_background(chorus_mesh_s* m, const chorus_params* P, int64
 // Right-hand side of the almost-flux-balance equations (Section 4.3) for y = (rho_0, p_0).
 struct AfbRhs {
   PhysArg<double> ph;
-  double Tc, Cp, L, kappa, kappa_r, gamma, GM;
+  double Tc, Cp, L, kappa, kappa_r, kappa_r1, kappa_r2, gamma, GM;
   void operator()(double r, const double y[2], double dy[2]) const {
     const double chi = ph.chi_c + ph.chi_ad / r;
     const double rho_a = ph.rho_c * std::pow(chi, ph.poly_n);
     const double T_a = Tc * chi, dT_a = -Tc * ph.chi_ad / (r * r);
     // the thermal balance integrated once with outward luminosity L (superadiabatic: Gamma < 0)
-    const double Gamma = -(L / (4.0 * kPi * r * r) + rho_a * Cp * kappa_r * dT_a) / (rho_a * T_a * kappa);
+    const double kr = kappa_r + (kappa_r1 + kappa_r2 * r) * r;
+    const double Gamma = -(L / (4.0 * kPi * r * r) + rho_a * Cp * kr * dT_a) / (rho_a * T_a * kappa);
     const double g = GM / (r * r);
     dy[0] = -y[0] * (Gamma / Cp + g * y[0] / (gamma * y[1]));
     dy[1] = -y[0] * g;
@@ -666,6 +721,8 @@ chorus_status chorus_afb_profile(const chorus_params* P, double r_inner, double 
   f.L = 4.0 * AfbRhs::kPi * r_inner * r_inner * P->bottom_flux;
   f.kappa = P->kappa;
   f.kappa_r = P->kappa_r;
+  f.kappa_r1 = P->kappa_r1;
+  f.kappa_r2 = P->kappa_r2;
   f.gamma = P->gamma;
   f.GM = P->GM;
   // grid r_j = r0 + j h; integrate from the middle radius r_m of the shell through the grid points on
@@ -711,6 +768,8 @@ chorus_status chorus_residual(chorus_mesh m, const chorus_params* P, chorus_prec
   if (!m || !Q || !R || !workspace || !params_ok(P)) return CHORUS_EINVAL;
   cudaStream_t st = (cudaStream_t)stream;
   if (prec == CHORUS_FP64) {
+    const chorus_status ks = ensure_kr(m, *P, st);
+    if (ks != CHORUS_OK) return ks;
     const PhysArg<double> ph = phys_arg<double>(*P, m->r_inner, m->r_outer);
     const MeshArg<double> ma = mesh_arg<double>(m);
     Ws<double> w = split_ws<double>(m, workspace);
@@ -816,6 +875,8 @@ chorus_status chorus_rk_step_scheme(chorus_mesh m, const chorus_params* P, choru
   if (n_steps == 0) return CHORUS_OK;
   cudaStream_t st = (cudaStream_t)stream;
   if (prec == CHORUS_FP64) {
+    const chorus_status ks = ensure_kr(m, *P, st);
+    if (ks != CHORUS_OK) return ks;
     const PhysArg<double> ph = phys_arg<double>(*P, m->r_inner, m->r_outer);
     const MeshArg<double> ma = mesh_arg<double>(m);
     Ws<double> w = split_ws<double>(m, workspace);
@@ -1141,6 +1202,8 @@ extern "C" chorus_status chorus_residual_noalloc(chorus_mesh m, const chorus_par
   if (s != CHORUS_OK) return s;
   cudaStream_t st = (cudaStream_t)stream;
   if (prec == CHORUS_FP64) {
+    const chorus_status ks = ensure_kr(m, *P, st);
+    if (ks != CHORUS_OK) return ks;
     const PhysArg<double> ph = phys_arg<double>(*P, m->r_inner, m->r_outer);
     const MeshArg<double> ma = mesh_arg<double>(m);
     double* T = (double*)scratch;

@@ -39,6 +39,8 @@ struct MeshArg {
   const R* Sf;       // [E][3 d][3 n][N+1 f][N*N line]  S^d_n = |J| d xi_d / d x_n at the d-flux points
   const R* invJ;     // [E][N^3] 1/|J| at the solution points
   const R* x;        // [E][3][N^3] solution-point coordinates
+  const R* kr;       // [E][3 d][N+1 f][N*N line] radiative diffusivity at the d-flux points, or null:
+                     // the constant kappa_r
 };
 
 // Background tables of the perturbation path (float, from FP64 computations).

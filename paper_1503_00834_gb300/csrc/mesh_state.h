@@ -50,6 +50,11 @@ struct chorus_mesh_s {
   std::vector<Rec> recs;
   std::vector<cudaEvent_t> pool;
   // attached learned closure (p = 2 meshes): record pointer and its per-stage output buffer
+  // radial radiative-diffusivity profile at the flux points (active when the params vary it)
+  bool kr_active = false;
+  double kr_coef[3] = {0, 0, 0};
+  double* d_kr64 = nullptr;
+  float* d_kr32 = nullptr;
   // well-balanced perturbation residual: R(Q0) is left out, so the discrete background is steady
   bool well_balanced = false;
   const void* closure = nullptr;

@@ -139,7 +139,7 @@ __device__ __forceinline__ R sig(const R g[kG], int a, int b) {
 // gr0: background density gradient (perturbation form only).
 template <bool PERT, class R>
 __device__ __forceinline__ void flux_visc(const Pt<R>& st, const R g[kG], const R gr0[3], R rho0, R p0,
-                                          const R s[3], const PhysArg<R>& ph, R Fv[5]) {
+                                          const R s[3], const PhysArg<R>& ph, R kr, R Fv[5]) {
   const R mu = st.rho * ph.nu;
   R ts[3];
 #pragma unroll
@@ -152,7 +152,7 @@ __device__ __forceinline__ void flux_visc(const Pt<R>& st, const R g[kG], const 
   for (int b = 0; b < 3; ++b) {
     R A = pr * g[b];
     if (PERT) A += dpr * gr0[b];
-    const R fb = -ph.CpR * (ph.kappa * (g[9 + b] / ph.gamma - A) + ph.kappa_r * (g[9 + b] - A));
+    const R fb = -ph.CpR * (ph.kappa * (g[9 + b] / ph.gamma - A) + kr * (g[9 + b] - A));
     fs += fb * s[b];
   }
   Fv[0] = R(0);

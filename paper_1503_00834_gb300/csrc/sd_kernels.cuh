@@ -67,6 +67,15 @@ __device__ __forceinline__ int line_sidx(int ln, int s) {
 // compiler (register cap).
 constexpr bool kResidBgShared = true;
 constexpr int kResidMinBlocksF32 = 3;
+// Orders with N >= 5 hold more line state than the FP32 register budget of N <= 4 allows: their
+// resident-CTA requests and whether the gradient lines sit in registers are set separately.
+constexpr int kResidMinBlocksLarge = 3;
+constexpr int kGradMinBlocksLarge = 4;
+constexpr bool kRegGradLarge = true;
+template <int N>
+constexpr int resid_min_blocks() { return N <= 4 ? kResidMinBlocksF32 : kResidMinBlocksLarge; }
+template <int N>
+constexpr int grad_min_blocks() { return N <= 4 ? 4 : kGradMinBlocksLarge; }
 
 // RES: the residual kernel's layout (it reads the 12-entry gradient record instead of lifting, so the
 // gradient array holds kG components; the lifting kernel needs 15).
@@ -225,6 +234,16 @@ __device__ __forceinline__ void flux_prefetch(const KArgs<R>& A, int e, int ln, 
     p.nb[0] = load_nb<N, PERT, true>(A, e, 2 * D, ln);
     p.nb[1] = load_nb<N, PERT, true>(A, e, 2 * D + 1, ln);
   }
+}
+
+// Radiative diffusivity at flux point f of line ln (direction D): from the mesh's flux-point table
+// (the interpolant of its solution-point values) when a profile is active, else the constant.  KR
+// false compiles the lookup out (the FP32 kernels are built both ways).
+template <int N, int D, bool KR, class R>
+__device__ __forceinline__ R kr_at(const KArgs<R>& A, int e, int ln, int f) {
+  if constexpr (!KR) return A.ph.kappa_r;
+  if (A.m.kr == nullptr) return A.ph.kappa_r;
+  return __ldg(A.m.kr + (((size_t)e * 3 + D) * (N + 1) + f) * (N * N) + ln);
 }
 
 // ------------------------------------------------------------------ trace kernel
@@ -462,7 +481,7 @@ struct FluxPointData {
 
 // Lifted gradients, then the one-sided normal viscous flux F_v . n_out on every face point,
 // written for the neighbours: Tv[e][F][0..2] = tau n, Tv[e][F][3] = u.tau n - f.n.
-template <int N, bool PERT, class R, int EPB, int D>
+template <int N, bool PERT, class R, int EPB, int D, bool KR>
 __device__ __forceinline__ void face_visc_dir(const KArgs<R>& A, const R* sm, int el, int ln, int e,
                                               const R (&s3f)[2][3]) {
   using L = Layout<N, PERT, R, EPB>;
@@ -524,7 +543,7 @@ __device__ __forceinline__ void face_visc_dir(const KArgs<R>& A, const R* sm, in
     const R nh[3] = {sgn * s3[0] / mag, sgn * s3[1] / mag, sgn * s3[2] / mag};
     const Pt<R> st = point_state<PERT>(qf, rho0f, E0f, A.ph);
     R Fv[5];
-    flux_visc<PERT>(st, gf, gr0f, rho0f, A.ph.gm1 * E0f, nh, A.ph, Fv);
+    flux_visc<PERT>(st, gf, gr0f, rho0f, A.ph.gm1 * E0f, nh, A.ph, kr_at<N, D, KR>(A, e, ln, f), Fv);
     R* o = A.Tv_out + ((size_t)e * 6 + 2 * D + side) * 4 * N2;
 #pragma unroll
     for (int v = 0; v < 4; ++v) o[v * N2 + ln] = Fv[1 + v];
@@ -532,8 +551,8 @@ __device__ __forceinline__ void face_visc_dir(const KArgs<R>& A, const R* sm, in
 }
 
 // FP32: four resident CTAs per SM (register cap 128; the shared memory of the lifting fits four)
-template <int N, bool PERT, class R, int EPB>
-__global__ void __launch_bounds__(EPB * N * N, sizeof(R) == 4 ? 4 : 1) k_grad(const KArgs<R> A) {
+template <int N, bool PERT, class R, int EPB, bool KR>
+__global__ void __launch_bounds__(EPB * N * N, sizeof(R) == 4 ? grad_min_blocks<N>() : 1) k_grad(const KArgs<R> A) {
   constexpr int N2 = N * N;
   extern __shared__ __align__(128) unsigned char smem_raw[];
   __shared__ __align__(8) uint64_t bar;
@@ -570,9 +589,9 @@ __global__ void __launch_bounds__(EPB * N * N, sizeof(R) == 4 ? 4 : 1) k_grad(co
       A.G_out[(size_t)e0 * kG * N3 + i] = sm[L::oG + (i / (kG * N3)) * L::SG + i % (kG * N3)];
   }
   if (!active || A.Tv_out == nullptr) return;
-  face_visc_dir<N, PERT, R, EPB, 0>(A, sm, el, ln, e, s3f[0]);
-  face_visc_dir<N, PERT, R, EPB, 1>(A, sm, el, ln, e, s3f[1]);
-  face_visc_dir<N, PERT, R, EPB, 2>(A, sm, el, ln, e, s3f[2]);
+  face_visc_dir<N, PERT, R, EPB, 0, KR>(A, sm, el, ln, e, s3f[0]);
+  face_visc_dir<N, PERT, R, EPB, 1, KR>(A, sm, el, ln, e, s3f[1]);
+  face_visc_dir<N, PERT, R, EPB, 2, KR>(A, sm, el, ln, e, s3f[2]);
 }
 
 // ------------------------------------------------------------------ flux sweep, one direction
@@ -580,7 +599,7 @@ __global__ void __launch_bounds__(EPB * N * N, sizeof(R) == 4 ? 4 : 1) k_grad(co
 // Transformed fluxes at the N+1 flux points of the thread's D-line (Eq. 12), common fluxes at
 // the two ends (Rusanov + averaged viscous; walls per Section 5), derivative back to the solution
 // points (Eq. 18), accumulated into the divergence array.
-template <int N, bool PERT, class R, int EPB, int D>
+template <int N, bool PERT, class R, int EPB, int D, bool KR>
 __device__ __forceinline__ void flux_dir(const KArgs<R>& A, R* sm, int el, int ln, int e, const FluxPre<R>& pre) {
   using L = Layout<N, PERT, R, EPB, true>;
   constexpr int N2 = N * N, N3 = N * N * N;
@@ -593,7 +612,7 @@ __device__ __forceinline__ void flux_dir(const KArgs<R>& A, R* sm, int el, int l
 
   // line data in registers (FP32); the FP64 form re-reads the gradients from shared memory per
   // flux point to stay within the register file
-  constexpr bool kRegGrad = sizeof(R) == 4;
+  constexpr bool kRegGrad = sizeof(R) == 4 && (N <= 4 || kRegGradLarge);
   R qv[5][N], gv[kRegGrad ? kG : 1][N];
 #pragma unroll
   for (int v = 0; v < 5; ++v) load_line_lin<N, D>(sq + v * N3, ln, qv[v]);
@@ -675,11 +694,12 @@ __device__ __forceinline__ void flux_dir(const KArgs<R>& A, R* sm, int el, int l
     }
     const Pt<R> st = point_state<PERT>(P.q, P.r0, P.E0, ph);
     const R p0f = ph.gm1 * P.E0;
+    const R krf = kr_at<N, D, KR>(A, e, ln, f);
     R Ft[5];
     if (f > 0 && f < N) {
       R Fi[5], Fv[5];
       flux_inv(P.q, st, s3, Fi);
-      flux_visc<PERT>(st, P.g, P.gr0, P.r0, p0f, s3, ph, Fv);
+      flux_visc<PERT>(st, P.g, P.gr0, P.r0, p0f, s3, ph, krf, Fv);
 #pragma unroll
       for (int v = 0; v < 5; ++v) Ft[v] = Fi[v] - Fv[v];
     } else {
@@ -694,7 +714,7 @@ __device__ __forceinline__ void flux_dir(const KArgs<R>& A, R* sm, int el, int l
         const Pt<R> sR = point_state<PERT>(nb.q, nb.r0, nb.E0, ph);
         rusanov<PERT>(P.q, st, P.r0, P.E0, nb.q, sR, nb.r0, nb.E0, nh, ph, Fh);
         R Fv[5];
-        flux_visc<PERT>(st, P.g, P.gr0, P.r0, p0f, nh, ph, Fv);
+        flux_visc<PERT>(st, P.g, P.gr0, P.r0, p0f, nh, ph, krf, Fv);
 #pragma unroll
         for (int v = 1; v < 5; ++v)  // the neighbour stored F_v . n_out(neighbour) = -F_v . n
           Fh[v] -= R(0.5) * (Fv[v] - nb.tv[v - 1]);
@@ -716,7 +736,7 @@ __device__ __forceinline__ void flux_dir(const KArgs<R>& A, R* sm, int el, int l
 #pragma unroll
           for (int b = 0; b < 3; ++b)
             fn += -ph.CpR *
-                  (ph.kappa * (P.g[9 + b] / ph.gamma - RT * P.g[b]) + ph.kappa_r * (P.g[9 + b] - RT * P.g[b])) *
+                  (ph.kappa * (P.g[9 + b] / ph.gamma - RT * P.g[b]) + krf * (P.g[9 + b] - RT * P.g[b])) *
                   nh[b];
           Fh[4] = fn;
         } else {
@@ -747,8 +767,8 @@ __device__ __forceinline__ void flux_dir(const KArgs<R>& A, R* sm, int el, int l
 // ------------------------------------------------------------------ residual kernel
 
 // FP32: ask for three resident CTAs per SM (register cap ~168 per thread)
-template <int N, bool PERT, class R, int EPB, int MODE>
-__global__ void __launch_bounds__(EPB * N * N, sizeof(R) == 4 ? kResidMinBlocksF32 : 1) k_resid(const KArgs<R> A) {
+template <int N, bool PERT, class R, int EPB, int MODE, bool KR>
+__global__ void __launch_bounds__(EPB * N * N, sizeof(R) == 4 ? resid_min_blocks<N>() : 1) k_resid(const KArgs<R> A) {
   using L = Layout<N, PERT, R, EPB, true>;
   constexpr int N2 = N * N, N3 = N * N * N;
   extern __shared__ __align__(128) unsigned char smem_raw[];
@@ -768,16 +788,16 @@ __global__ void __launch_bounds__(EPB * N * N, sizeof(R) == 4 ? kResidMinBlocksF
   });
   __syncthreads();
   if (active) {
-    flux_dir<N, PERT, R, EPB, 0>(A, sm, el, ln, e, fp);
+    flux_dir<N, PERT, R, EPB, 0, KR>(A, sm, el, ln, e, fp);
     flux_prefetch<N, PERT, R, 1>(A, e, ln, fp);
   }
   __syncthreads();
   if (active) {
-    flux_dir<N, PERT, R, EPB, 1>(A, sm, el, ln, e, fp);
+    flux_dir<N, PERT, R, EPB, 1, KR>(A, sm, el, ln, e, fp);
     flux_prefetch<N, PERT, R, 2>(A, e, ln, fp);
   }
   __syncthreads();
-  if (active) flux_dir<N, PERT, R, EPB, 2>(A, sm, el, ln, e, fp);
+  if (active) flux_dir<N, PERT, R, EPB, 2, KR>(A, sm, el, ln, e, fp);
 
   // Global inputs of the epilogue, all issued before its first store.  The epilogue works point by
   // point, so thread ln takes the points ln + N^2 i (i < N): 16 consecutive threads read 64
@@ -879,9 +899,19 @@ struct Launch {
   static cudaError_t grad(const KArgs<R>& A, cudaStream_t st) {
     if (A.m.E == 0) return cudaSuccess;
     const size_t sm = (size_t)L::total_grad * sizeof(R);
-    cudaError_t e = cudaFuncSetAttribute(k_grad<N, PERT, R, EPB>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    // the radiative-diffusivity profile is a compile-time option of the FP32 kernels (FP64 checks it
+    // at run time)
+    if constexpr (sizeof(R) == 8) {
+      return grad_kr<true>(A, st, sm);
+    } else {
+      return A.m.kr != nullptr ? grad_kr<true>(A, st, sm) : grad_kr<false>(A, st, sm);
+    }
+  }
+  template <bool KR>
+  static cudaError_t grad_kr(const KArgs<R>& A, cudaStream_t st, size_t sm) {
+    cudaError_t e = cudaFuncSetAttribute(k_grad<N, PERT, R, EPB, KR>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
     if (e != cudaSuccess) return e;
-    k_grad<N, PERT, R, EPB><<<blocks(A.m.E), threads, sm, st>>>(A);
+    k_grad<N, PERT, R, EPB, KR><<<blocks(A.m.E), threads, sm, st>>>(A);
     return cudaGetLastError();
   }
   template <int MODE>
@@ -889,10 +919,18 @@ struct Launch {
     if (A.m.E == 0) return cudaSuccess;
     if (A.G_in == nullptr) return cudaErrorInvalidValue;  // the residual kernel reads the gradient record
     const size_t sm = (size_t)Layout<N, PERT, R, EPB, true>::total_resid * sizeof(R);
+    if constexpr (sizeof(R) == 8) {
+      return resid_kr<MODE, true>(A, st, sm);
+    } else {
+      return A.m.kr != nullptr ? resid_kr<MODE, true>(A, st, sm) : resid_kr<MODE, false>(A, st, sm);
+    }
+  }
+  template <int MODE, bool KR>
+  static cudaError_t resid_kr(const KArgs<R>& A, cudaStream_t st, size_t sm) {
     cudaError_t e =
-        cudaFuncSetAttribute(k_resid<N, PERT, R, EPB, MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+        cudaFuncSetAttribute(k_resid<N, PERT, R, EPB, MODE, KR>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
     if (e != cudaSuccess) return e;
-    k_resid<N, PERT, R, EPB, MODE><<<blocks(A.m.E), threads, sm, st>>>(A);
+    k_resid<N, PERT, R, EPB, MODE, KR><<<blocks(A.m.E), threads, sm, st>>>(A);
     return cudaGetLastError();
   }
 };

@@ -60,7 +60,7 @@ class Params(ctypes.Structure):
     """chorus_params (all doubles, in header order)."""
 
     _fields_ = [(n, ctypes.c_double) for n in ("gamma", "R_gas", "GM", "Omega", "nu", "kappa", "kappa_r", "poly_n",
-                                                "N_rho", "rho_c", "bottom_flux", "T_top")]
+                                                "N_rho", "rho_c", "bottom_flux", "T_top", "kappa_r1", "kappa_r2")]
 
     @classmethod
     def from_phys(cls, phys) -> "Params":

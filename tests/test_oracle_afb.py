@@ -62,3 +62,19 @@ def test_target_gradient_closed_form_and_radiative_term():
     # dT_a/dr against a finite difference of T_a
     h = 1e-6
     assert np.allclose(afb.dT_a_dr(ph, r), (ph.T_a(r + h) - ph.T_a(r - h)) / (2 * h), rtol=1e-8)
+
+
+def test_solar_radiative_profile_carries_the_luminosity_at_the_bottom():
+    """The Section 7.2 choice of lambda: the radiative flux equals L/(4 pi r_i^2) at r_i, so the
+    target entropy gradient vanishes there; above it the layer is superadiabatic."""
+    from chorus_inputs import paper_case_phys
+
+    beta, phys = paper_case_phys("sun")
+    ph = Physics.from_params(phys, beta, 1.0)
+    assert ph.kappa_r_varies
+    G = afb.target_entropy_gradient(ph, np.array([beta, 0.8, 0.9, 1.0]))
+    G_scale = abs(afb.luminosity(ph)) / (4 * math.pi * beta ** 2 * ph.rho_a(beta) * ph.T_a(beta) * ph.kappa)
+    assert abs(G[0]) < 1e-10 * G_scale
+    assert np.all(G[1:] < 0)
+    r = np.linspace(beta, 1.0, 50)
+    assert np.all(ph.kappa_r_at(r) > 0)
