@@ -58,6 +58,20 @@ __device__ __forceinline__ bool mbar_wait0(uint64_t* bar, unsigned* err) {
   return false;
 }
 
+// ------------------------------------------------------------------ division
+
+// Quotients of the point physics.  FP64: the correctly rounded quotient.  FP32 (the perturbation
+// form, whose tolerance is relative 1e-5): with kFastDivF32 the approximate quotient __fdividef
+// (reciprocal and product, error of a few ulp for divisors of normal magnitude) instead of the
+// correctly rounded division sequence.
+constexpr bool kFastDivF32 = true;
+
+template <class R>
+__device__ __forceinline__ R qdiv(R a, R b) {
+  if constexpr (sizeof(R) == 4 && kFastDivF32) return __fdividef(a, b);
+  else return a / b;
+}
+
 // ------------------------------------------------------------------ index helpers
 
 // point index of position s along line `ln` of direction d
@@ -97,7 +111,7 @@ __device__ __forceinline__ Pt<R> point_state(const R q[5], R rho0, R E0, const P
   Pt<R> s;
   s.rhop = q[0];
   s.rho = PERT ? rho0 + q[0] : q[0];
-  const R ir = R(1) / s.rho;
+  const R ir = qdiv(R(1), s.rho);
   s.u[0] = q[1] * ir;
   s.u[1] = q[2] * ir;
   s.u[2] = q[3] * ir;
@@ -144,15 +158,15 @@ __device__ __forceinline__ void flux_visc(const Pt<R>& st, const R g[kG], const 
   R ts[3];
 #pragma unroll
   for (int a = 0; a < 3; ++a) ts[a] = mu * (sig(g, a, 0) * s[0] + sig(g, a, 1) * s[1] + sig(g, a, 2) * s[2]);
-  const R pr = st.ptot / st.rho;
+  const R pr = qdiv(st.ptot, st.rho);
   R dpr = R(0);
-  if (PERT) dpr = (st.p * rho0 - p0 * st.rhop) / (st.rho * rho0);  // p/rho - p0/rho0
+  if (PERT) dpr = qdiv(st.p * rho0 - p0 * st.rhop, st.rho * rho0);  // p/rho - p0/rho0
   R fs = R(0);
 #pragma unroll
   for (int b = 0; b < 3; ++b) {
     R A = pr * g[b];
     if (PERT) A += dpr * gr0[b];
-    const R fb = -ph.CpR * (ph.kappa * (g[9 + b] / ph.gamma - A) + kr * (g[9 + b] - A));
+    const R fb = -ph.CpR * (ph.kappa * (qdiv(g[9 + b], ph.gamma) - A) + kr * (g[9 + b] - A));
     fs += fb * s[b];
   }
   Fv[0] = R(0);
@@ -173,7 +187,7 @@ __device__ __forceinline__ void grad_prim(const Pt<R>& st, const R gq[15], const
     grt[n] = PERT ? gr0[n] + gq[n] : gq[n];
     g[n] = gq[n];
   }
-  const R ir = R(1) / st.rho;
+  const R ir = qdiv(R(1), st.rho);
   R gu[3][3];
 #pragma unroll
   for (int a = 0; a < 3; ++a)
@@ -199,16 +213,16 @@ __device__ __forceinline__ void rusanov(const R qL[5], const Pt<R>& sL, R rho0L,
   R FL[5], FR[5];
   flux_inv(qL, sL, n, FL);
   flux_inv(qR, sR, n, FR);
-  const R cL = sqrt(ph.gamma * sL.ptot / sL.rho);
-  const R cR = sqrt(ph.gamma * sR.ptot / sR.rho);
+  const R cL = sqrt(qdiv(ph.gamma * sL.ptot, sL.rho));
+  const R cR = sqrt(qdiv(ph.gamma * sR.ptot, sR.rho));
   const R vL = fabs(sL.u[0] * n[0] + sL.u[1] * n[1] + sL.u[2] * n[2]) + cL;
   const R vR = fabs(sR.u[0] * n[0] + sR.u[1] * n[1] + sR.u[2] * n[2]) + cR;
   const R lam = vL > vR ? vL : vR;
 #pragma unroll
   for (int v = 0; v < 5; ++v) F[v] = R(0.5) * (FL[v] + FR[v]) - R(0.5) * lam * (qR[v] - qL[v]);
   if (PERT) {
-    const R c0L = sqrt(ph.gamma * ph.gm1 * E0L / rho0L);
-    const R c0R = sqrt(ph.gamma * ph.gm1 * E0R / rho0R);
+    const R c0L = sqrt(qdiv(ph.gamma * ph.gm1 * E0L, rho0L));
+    const R c0R = sqrt(qdiv(ph.gamma * ph.gm1 * E0R, rho0R));
     const R lam0 = c0L > c0R ? c0L : c0R;
     F[0] -= R(0.5) * (lam - lam0) * (rho0R - rho0L);
     F[4] -= R(0.5) * (lam - lam0) * (E0R - E0L);

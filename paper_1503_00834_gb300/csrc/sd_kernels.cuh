@@ -67,15 +67,18 @@ __device__ __forceinline__ int line_sidx(int ln, int s) {
 // compiler (register cap).
 constexpr bool kResidBgShared = true;
 constexpr int kResidMinBlocksF32 = 3;
-// Orders with N >= 5 hold more line state than the FP32 register budget of N <= 4 allows: their
-// resident-CTA requests and whether the gradient lines sit in registers are set separately.
-constexpr int kResidMinBlocksLarge = 3;
-constexpr int kGradMinBlocksLarge = 4;
-constexpr bool kRegGradLarge = true;
+// Per order, from timings of every combination on the 786,432-element p = 4 and the 98,304-element
+// p = 5 shells: the resident CTAs asked of the compiler for the residual and the lifting kernel, and
+// whether the flux sweep holds the line's gradient record in registers (else it reads it from
+// shared memory per flux point).  N = 6 runs two CTAs of four elements per SM (shared memory) and
+// does best with the registers that allows; N = 5 keeps the N <= 4 requests, with the gradient lines
+// in shared memory.
 template <int N>
-constexpr int resid_min_blocks() { return N <= 4 ? kResidMinBlocksF32 : kResidMinBlocksLarge; }
+__host__ __device__ constexpr int resid_min_blocks() { return N <= 5 ? kResidMinBlocksF32 : 2; }
 template <int N>
-constexpr int grad_min_blocks() { return N <= 4 ? 4 : kGradMinBlocksLarge; }
+__host__ __device__ constexpr int grad_min_blocks() { return N <= 5 ? 4 : 2; }
+template <int N>
+__host__ __device__ constexpr bool reg_grad_lines() { return N <= 4; }
 
 // RES: the residual kernel's layout (it reads the 12-entry gradient record instead of lifting, so the
 // gradient array holds kG components; the lifting kernel needs 15).
@@ -168,15 +171,34 @@ struct NbFace {
   R r0, E0;
 };
 
+// Where the neighbour's face block of face F of element e sits: bf = neighbour * 6 + its face (or the
+// wall code -1 / -2), tp = the neighbour's face-point index of own face point ln.
+struct NbIdx {
+  int bf, tp;
+};
+
+template <int N, class R>
+__device__ __forceinline__ NbIdx nb_index(const KArgs<R>& A, int e, int F, int ln) {
+  NbIdx x;
+  const int k = __ldg(A.m.nbr + e * 6 + F);
+  x.bf = k;
+  x.tp = 0;
+  if (k >= 0) {
+    const int c = __ldg(A.m.code + e * 6 + F);
+    x.bf = k * 6 + (c >> 3);
+    x.tp = map_face_pt<N>(ln, c & 7);
+  }
+  return x;
+}
+
 template <int N, bool PERT, bool WANT_TV, class R>
-__device__ __forceinline__ NbFace<R> load_nb(const KArgs<R>& A, int e, int F, int ln) {
+__device__ __forceinline__ NbFace<R> load_nb_at(const KArgs<R>& A, NbIdx x) {
   constexpr int N2 = N * N;
   NbFace<R> f;
-  f.kind = __ldg(A.m.nbr + e * 6 + F);
-  if (f.kind >= 0) {
-    const int c = __ldg(A.m.code + e * 6 + F);
-    const int tp = map_face_pt<N>(ln, c & 7);
-    const size_t base = (size_t)f.kind * 6 + (c >> 3);
+  f.kind = x.bf;
+  if (x.bf >= 0) {
+    const size_t base = (size_t)x.bf;
+    const int tp = x.tp;
 #pragma unroll
     for (int v = 0; v < 5; ++v) f.q[v] = __ldg(A.T + (base * 5 + v) * N2 + tp);
     if (WANT_TV) {
@@ -191,6 +213,11 @@ __device__ __forceinline__ NbFace<R> load_nb(const KArgs<R>& A, int e, int F, in
   return f;
 }
 
+template <int N, bool PERT, bool WANT_TV, class R>
+__device__ __forceinline__ NbFace<R> load_nb(const KArgs<R>& A, int e, int F, int ln) {
+  return load_nb_at<N, PERT, WANT_TV>(A, nb_index<N>(A, e, F, ln));
+}
+
 // Global-memory inputs of one direction sweep, loaded ahead of their use so that their latency
 // overlaps the preceding work (the sweeps otherwise stall on them once per flux point).
 template <int N, class R>
@@ -202,8 +229,8 @@ struct LiftPre {
 
 template <class R>
 struct FluxPre {
-  R s3[3];  // S^D_n at flux point 1 of the line (the first one the sweep visits)
-  NbFace<R> nb[2];
+  R s3[3];       // S^D_n at flux point 1 of the line (the first one the sweep visits)
+  NbIdx nbi[2];  // where the neighbour data of the two end points sit
 };
 
 template <int N, bool PERT, class R, int D>
@@ -220,9 +247,13 @@ __device__ __forceinline__ void lift_prefetch(const KArgs<R>& A, int e, int ln, 
   p.nb[1] = load_nb<N, PERT, false>(A, e, 2 * D + 1, ln);
 }
 
-// Whether the flux sweep's neighbour data are loaded ahead (registers held through the sweep) or at
-// the two end points.
-constexpr bool kFluxNbAhead = false;
+// How the flux sweep gets the neighbour data of its two end points: 0 = index and data loaded at
+// the end point; 1 = index (neighbour, face, orientation) loaded with the sweep's first metrics, data
+// at the end point; 2 = as 1, and the data of each end point issued one flux point ahead.  Timed per
+// order: 2 is fastest for N = 3, 5, 6; at N = 4 the registers it holds through the sweep spill and
+// 0 is fastest.
+template <int N>
+__host__ __device__ constexpr int flux_nb_mode() { return N == 4 ? 0 : 2; }
 
 template <int N, bool PERT, class R, int D>
 __device__ __forceinline__ void flux_prefetch(const KArgs<R>& A, int e, int ln, FluxPre<R>& p) {
@@ -230,9 +261,9 @@ __device__ __forceinline__ void flux_prefetch(const KArgs<R>& A, int e, int ln, 
   const R* Sl = A.m.Sf + ((size_t)e * 3 + D) * 3 * (N + 1) * N2;
 #pragma unroll
   for (int n = 0; n < 3; ++n) p.s3[n] = __ldg(Sl + (n * (N + 1) + 1) * N2 + ln);  // flux point 1
-  if (kFluxNbAhead) {
-    p.nb[0] = load_nb<N, PERT, true>(A, e, 2 * D, ln);
-    p.nb[1] = load_nb<N, PERT, true>(A, e, 2 * D + 1, ln);
+  if (flux_nb_mode<N>() >= 1) {
+    p.nbi[0] = nb_index<N>(A, e, 2 * D, ln);
+    p.nbi[1] = nb_index<N>(A, e, 2 * D + 1, ln);
   }
 }
 
@@ -372,12 +403,13 @@ __device__ __forceinline__ void lift_dir(const KArgs<R>& A, R* sm, int el, int l
       // or p = R rho T_top (outer wall)
       const R sg_ = side ? R(1) : R(-1);
       const R mag = sqrt(S[0][f] * S[0][f] + S[1][f] * S[1][f] + S[2][f] * S[2][f]);
-      const R nh[3] = {sg_ * S[0][f] / mag, sg_ * S[1][f] / mag, sg_ * S[2][f] / mag};
+      const R im = qdiv(sg_, mag);
+      const R nh[3] = {im * S[0][f], im * S[1][f], im * S[2][f]};
       const Pt<R> st = point_state<PERT>(qe, rho0e, E0e, ph);
       const R mn = qe[1] * nh[0] + qe[2] * nh[1] + qe[3] * nh[2];
       const R mc[3] = {qe[1] - mn * nh[0], qe[2] - mn * nh[1], qe[3] - mn * nh[2]};
       const R pc = nb.kind == -2 ? ph.Rgas * st.rhop * ph.T_top : st.p;
-      const R Ec = pc / ph.gm1 + R(0.5) * (mc[0] * mc[0] + mc[1] * mc[1] + mc[2] * mc[2]) / st.rho;
+      const R Ec = qdiv(pc, ph.gm1) + qdiv(R(0.5) * (mc[0] * mc[0] + mc[1] * mc[1] + mc[2] * mc[2]), st.rho);
       dq[0][side] = R(0);
       dq[1][side] = mc[0] - qe[1];
       dq[2][side] = mc[1] - qe[2];
@@ -540,7 +572,8 @@ __device__ __forceinline__ void face_visc_dir(const KArgs<R>& A, const R* sm, in
     for (int n = 0; n < 3; ++n) s3[n] = side ? s3f[1][n] : s3f[0][n];
     const R sgn = side ? R(1) : R(-1);
     const R mag = sqrt(s3[0] * s3[0] + s3[1] * s3[1] + s3[2] * s3[2]);
-    const R nh[3] = {sgn * s3[0] / mag, sgn * s3[1] / mag, sgn * s3[2] / mag};
+    const R im = qdiv(sgn, mag);
+    const R nh[3] = {im * s3[0], im * s3[1], im * s3[2]};
     const Pt<R> st = point_state<PERT>(qf, rho0f, E0f, A.ph);
     R Fv[5];
     flux_visc<PERT>(st, gf, gr0f, rho0f, A.ph.gm1 * E0f, nh, A.ph, kr_at<N, D, KR>(A, e, ln, f), Fv);
@@ -612,7 +645,7 @@ __device__ __forceinline__ void flux_dir(const KArgs<R>& A, R* sm, int el, int l
 
   // line data in registers (FP32); the FP64 form re-reads the gradients from shared memory per
   // flux point to stay within the register file
-  constexpr bool kRegGrad = sizeof(R) == 4 && (N <= 4 || kRegGradLarge);
+  constexpr bool kRegGrad = sizeof(R) == 4 && reg_grad_lines<N>();
   R qv[5][N], gv[kRegGrad ? kG : 1][N];
 #pragma unroll
   for (int v = 0; v < 5; ++v) load_line_lin<N, D>(sq + v * N3, ln, qv[v]);
@@ -639,6 +672,8 @@ __device__ __forceinline__ void flux_dir(const KArgs<R>& A, R* sm, int el, int l
   // Flux points in the order 1, ..., N, 0, so that the neighbour data (prefetched) are first needed
   // after the interior points; S^D at the next flux point is loaded one iteration ahead.
   R s3n[3] = {pre.s3[0], pre.s3[1], pre.s3[2]};
+  NbFace<R> nbn;  // mode 2: the next end point's neighbour data
+  nbn.kind = -1;
 #pragma unroll 1
   for (int it = 0; it <= N; ++it) {
     const int f = it < N ? it + 1 : 0;
@@ -647,6 +682,11 @@ __device__ __forceinline__ void flux_dir(const KArgs<R>& A, R* sm, int el, int l
       const int fn = it + 1 < N ? it + 2 : 0;
 #pragma unroll
       for (int n = 0; n < 3; ++n) s3n[n] = __ldg(Sl + (n * (N + 1) + fn) * N2 + ln);
+    }
+    NbFace<R> nbc;  // mode 2: this end point's neighbour data
+    if (flux_nb_mode<N>() == 2) {
+      nbc = nbn;
+      if (it == N - 2 || it == N - 1) nbn = load_nb_at<N, PERT, true>(A, pre.nbi[it == N - 2 ? 1 : 0]);
     }
     R w[N];
 #pragma unroll
@@ -704,11 +744,13 @@ __device__ __forceinline__ void flux_dir(const KArgs<R>& A, R* sm, int el, int l
       for (int v = 0; v < 5; ++v) Ft[v] = Fi[v] - Fv[v];
     } else {
       const int side = (f == N);
-      const NbFace<R> nb = !kFluxNbAhead ? load_nb<N, PERT, true>(A, e, 2 * D + side, ln)
-                                         : (side ? pre.nb[1] : pre.nb[0]);
+      const NbFace<R> nb = flux_nb_mode<N>() == 0   ? load_nb<N, PERT, true>(A, e, 2 * D + side, ln)
+                           : flux_nb_mode<N>() == 1 ? load_nb_at<N, PERT, true>(A, pre.nbi[side])
+                                                    : nbc;
       const R sgn = side ? R(1) : R(-1);
       const R mag = sqrt(s3[0] * s3[0] + s3[1] * s3[1] + s3[2] * s3[2]);
-      const R nh[3] = {sgn * s3[0] / mag, sgn * s3[1] / mag, sgn * s3[2] / mag};
+      const R im = qdiv(sgn, mag);
+    const R nh[3] = {im * s3[0], im * s3[1], im * s3[2]};
       R Fh[5];
       if (nb.kind >= 0) {
         const Pt<R> sR = point_state<PERT>(nb.q, nb.r0, nb.E0, ph);
@@ -736,7 +778,7 @@ __device__ __forceinline__ void flux_dir(const KArgs<R>& A, R* sm, int el, int l
 #pragma unroll
           for (int b = 0; b < 3; ++b)
             fn += -ph.CpR *
-                  (ph.kappa * (P.g[9 + b] / ph.gamma - RT * P.g[b]) + krf * (P.g[9 + b] - RT * P.g[b])) *
+                  (ph.kappa * (qdiv(P.g[9 + b], ph.gamma) - RT * P.g[b]) + krf * (P.g[9 + b] - RT * P.g[b])) *
                   nh[b];
           Fh[4] = fn;
         } else {
@@ -834,7 +876,7 @@ __global__ void __launch_bounds__(EPB * N * N, sizeof(R) == 4 ? resid_min_blocks
       for (int v = 0; v < 5; ++v) q[v] = sq[v * N3 + pt];
       const R x0 = xg[0][i], x1 = xg[1][i], x2 = xg[2][i];
       const R r2 = x0 * x0 + x1 * x1 + x2 * x2;
-      const R gr = ph.GM / (r2 * sqrt(r2));  // g = gr * x points outward (the source uses -rho g_vec)
+      const R gr = qdiv(ph.GM, r2 * sqrt(r2));  // g = gr * x points outward (the source uses -rho g_vec)
       const R g3[3] = {gr * x0, gr * x1, gr * x2};
       R M[5];
       M[0] = R(0);
