@@ -65,6 +65,33 @@ def job_rate(world: int, units_per_rank: float, seconds: float) -> float:
     return world * units_per_rank / seconds
 
 
+def kernel_sources_digest() -> str:
+    """SHA-256 of the residual kernels' sources (the stepping kernels and their headers): the DRAM
+    counters in profiles/traffic.json are reported only for the sources they were taken on."""
+    import hashlib
+
+    csrc = os.path.join(ROOT, "paper_1503_00834_gb300", "csrc")
+    names = ["internal.h", "sd_device.cuh", "sd_kernels.cuh", "kern_inst.cuh"] + [f"kern_p{p}.cu" for p in (2, 3, 4, 5)]
+    h = hashlib.sha256()
+    for n in names:
+        with open(os.path.join(csrc, n), "rb") as f:
+            h.update(n.encode() + b"\0" + f.read())
+    return h.hexdigest()
+
+
+def lookup_traffic(path: str, kernel: str, workload: str, prec: str):
+    """DRAM bytes per launch of `kernel` on `workload` from an ncu summary file, or None when the file
+    is missing or its counters were taken on other kernel sources than the ones built here."""
+    try:
+        with open(path) as f:
+            tr = json.load(f)
+    except (OSError, ValueError):
+        return None
+    if tr.get("sources_sha256") != kernel_sources_digest():
+        return None
+    return tr.get(f"{kernel}:{workload}:{prec}")
+
+
 def _peaks():
     path = os.path.join(ROOT, "MEASURED_PEAKS.json")
     try:
@@ -368,16 +395,7 @@ def main():
     alg = (ALG_BYTES_PER_DOF_STAGE if prec == FP32_PERT else ALG_BYTES_PER_DOF_STAGE_FP64)[cfg.p]
     peak, peak_kind = _peaks()
     achieved = alg * n_dof / (per_launch_ms / 1e3) / 1e9
-    traffic = None
-    prof = os.path.join(ROOT, "profiles", "traffic.json")
-    if os.path.exists(prof):
-        try:
-            with open(prof) as f:
-                tr = json.load(f)
-            key = f"{names[dom]}:{cfg.name}:{args.prec}"
-            traffic = tr.get(key)
-        except Exception:
-            traffic = None
+    traffic = lookup_traffic(os.path.join(ROOT, "profiles", "traffic.json"), names[dom], cfg.name, args.prec)
 
     # ---- FP64 GPU path on the same workload (the metric compares both)
     fp64_value = None
