@@ -66,12 +66,14 @@ def job_rate(world: int, units_per_rank: float, seconds: float) -> float:
 
 
 def kernel_sources_digest() -> str:
-    """SHA-256 of the residual kernels' sources (the stepping kernels and their headers): the DRAM
-    counters in profiles/traffic.json are reported only for the sources they were taken on."""
+    """SHA-256 of the residual kernels' sources (the stepping kernels, their headers and the build
+    script with its per-source compiler options): the DRAM counters in profiles/traffic.json are
+    reported only for the sources they were taken on."""
     import hashlib
 
     csrc = os.path.join(ROOT, "paper_1503_00834_gb300", "csrc")
     names = ["internal.h", "sd_device.cuh", "sd_kernels.cuh", "kern_inst.cuh"] + [f"kern_p{p}.cu" for p in (2, 3, 4, 5)]
+    names.append(os.path.join("..", "build.py"))
     h = hashlib.sha256()
     for n in names:
         with open(os.path.join(csrc, n), "rb") as f:

@@ -5,10 +5,13 @@
 
 namespace chorus {
 
-template <int N, int EPB64, int EPB32>
+// EPB32R: elements per CTA of the FP32 residual kernel (by default those of the FP32 lifting kernel;
+// the two kernels share no shared-memory layout, only the per-element arrays in global memory).
+template <int N, int EPB64, int EPB32, int EPB32R = EPB32>
 struct Inst {
   using L64 = Launch<N, false, double, EPB64>;
   using L32 = Launch<N, true, float, EPB32>;
+  using L32R = Launch<N, true, float, EPB32R>;
 
   static cudaError_t trace64(const MeshArg<double>& m, const OpsArg<double>& ops, const double* q, double* T,
                              cudaStream_t st) {
@@ -58,7 +61,7 @@ struct Inst {
     A.G_in = G;
     set_rk(A, rk);
     A.dt = dt; A.err = err;
-    return mode == kModeRK ? L32::template resid<kModeRK>(A, st) : L32::template resid<kModeResidual>(A, st);
+    return mode == kModeRK ? L32R::template resid<kModeRK>(A, st) : L32R::template resid<kModeResidual>(A, st);
   }
   static LaunchSet set() { return LaunchSet{trace64, grad64, resid64, trace32, grad32, resid32, EPB32}; }
 };

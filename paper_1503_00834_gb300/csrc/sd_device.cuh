@@ -41,6 +41,17 @@ __device__ __forceinline__ void bulk_g2s(void* dst, const void* src, uint32_t by
       : "memory");
 }
 
+// 1D bulk copy shared -> global (bulk-group completion).  The shared data must have been written
+// before a fence.proxy.async by the writing threads and a barrier.
+__device__ __forceinline__ void bulk_s2g(void* dst, const void* src, uint32_t bytes) {
+  asm volatile("cp.async.bulk.global.shared::cta.bulk_group [%0], [%1], %2;" ::"l"(dst), "r"(smem_addr(src)), "r"(bytes)
+               : "memory");
+}
+__device__ __forceinline__ void bulk_commit() { asm volatile("cp.async.bulk.commit_group;" ::: "memory"); }
+// Wait until the committed bulk stores have read their shared-memory source (before the CTA exits).
+__device__ __forceinline__ void bulk_wait_read() { asm volatile("cp.async.bulk.wait_group.read 0;" ::: "memory"); }
+__device__ __forceinline__ void fence_async_smem() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
+
 // Bounded wait on phase 0 of the barrier.  Returns false (and sets *err) if the limit ran out.
 __device__ __forceinline__ bool mbar_wait0(uint64_t* bar, unsigned* err) {
   const uint32_t a = smem_addr(bar);

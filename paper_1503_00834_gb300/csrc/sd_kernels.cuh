@@ -73,12 +73,21 @@ constexpr int kResidMinBlocksF32 = 3;
 // shared memory per flux point).  N = 6 runs two CTAs of four elements per SM (shared memory) and
 // does best with the registers that allows; N = 5 keeps the N <= 4 requests, with the gradient lines
 // in shared memory.
-template <int N>
+template <int N, int EPB>
 __host__ __device__ constexpr int resid_min_blocks() { return N <= 5 ? kResidMinBlocksF32 : 2; }
 template <int N>
 __host__ __device__ constexpr int grad_min_blocks() { return N <= 5 ? 4 : 2; }
 template <int N>
 __host__ __device__ constexpr bool reg_grad_lines() { return N <= 4; }
+
+// Lifting order: false = directions 0, 1, 2 and a separate pass that forms the gradient record;
+// true = directions 1, 2, 0 with the record formed in the last sweep.
+constexpr bool kLiftFused = true;
+
+// Whether the lifting kernel writes the gradient record with bulk stores from shared memory (timed
+// per order: 1-4 % faster at N = 3, 4, 6, 3 % slower at N = 5).
+template <int N>
+__host__ __device__ constexpr bool grad_bulk_store() { return N != 5; }
 
 // RES: the residual kernel's layout (it reads the 12-entry gradient record instead of lifting, so the
 // gradient array holds kG components; the lifting kernel needs 15).
@@ -249,11 +258,12 @@ __device__ __forceinline__ void lift_prefetch(const KArgs<R>& A, int e, int ln, 
 
 // How the flux sweep gets the neighbour data of its two end points: 0 = index and data loaded at
 // the end point; 1 = index (neighbour, face, orientation) loaded with the sweep's first metrics, data
-// at the end point; 2 = as 1, and the data of each end point issued one flux point ahead.  Timed per
-// order: 2 is fastest for N = 3, 5, 6; at N = 4 the registers it holds through the sweep spill and
-// 0 is fastest.
+// at the end point; 2 = as 1, and the data of each end point issued one flux point ahead; 3 = the
+// element's six (neighbour, face code) pairs staged in shared memory with the state, data loaded at
+// the end point.  Timed per order: 2 is fastest for N = 3, 5, 6; at N = 4 the registers it holds
+// through the sweep spill.
 template <int N>
-__host__ __device__ constexpr int flux_nb_mode() { return N == 4 ? 0 : 2; }
+__host__ __device__ constexpr int flux_nb_mode() { return N == 4 ? 3 : 2; }
 
 template <int N, bool PERT, class R, int D>
 __device__ __forceinline__ void flux_prefetch(const KArgs<R>& A, int e, int ln, FluxPre<R>& p) {
@@ -355,10 +365,13 @@ __device__ __forceinline__ void stage_elements(const KArgs<R>& A, R* sm, uint64_
 
 // d q / d xi_D along the thread's D-line with common face values (BR1-like averaging, Section 3;
 // walls Section 5), times grad xi_D = S^D / |J|, accumulated into the gradient array.
-template <int N, bool PERT, class R, int EPB, int D>
+// FIRST: the sweep stores its contribution (no partial sums yet).  LAST: the sweep adds the partial
+// sums of the other two directions and turns the complete conserved gradients of its line's points
+// into the gradient record in place (its line's points are touched by no other thread in this phase).
+template <int N, bool PERT, class R, int EPB, int D, bool FIRST, bool LAST>
 __device__ __forceinline__ void lift_dir(const KArgs<R>& A, R* sm, int el, int ln, int e, const LiftPre<N, R>& pre) {
   using L = Layout<N, PERT, R, EPB>;
-  constexpr int N2 = N * N, N3 = N * N * N;
+  constexpr int N3 = N * N * N;
   const R* sq = sm + L::oQ + el * L::SQ;
   const R* sbg = sm + L::oBG + el * L::SBG;
   R* sg = sm + L::oG + el * L::SG;
@@ -417,6 +430,12 @@ __device__ __forceinline__ void lift_dir(const KArgs<R>& A, R* sm, int el, int l
       dq[4][side] = Ec - qe[4];
     }
   }
+  R g0[LAST && PERT ? 3 : 1][N];
+  if constexpr (LAST && PERT) {
+    const R* sgr0 = sm + L::oGR0 + el * L::SGR0;
+#pragma unroll
+    for (int n = 0; n < 3; ++n) load_line_lin<N, D>(sgr0 + n * N3, ln, g0[n]);
+  }
 #pragma unroll
   for (int i = 0; i < N; ++i) {
     const R ij = pre.ij[i];
@@ -429,6 +448,7 @@ __device__ __forceinline__ void lift_dir(const KArgs<R>& A, R* sm, int el, int l
       gx[n] = acc * ij;
     }
     const int si = line_sidx<N, D, R>(ln, i);
+    R gq[LAST ? 15 : 1];
 #pragma unroll
     for (int v = 0; v < 5; ++v) {
       R dv = A.ops.D[i][0] * dq[v][0] + A.ops.D[i][N] * dq[v][1];
@@ -437,33 +457,67 @@ __device__ __forceinline__ void lift_dir(const KArgs<R>& A, R* sm, int el, int l
 #pragma unroll
       for (int n = 0; n < 3; ++n) {
         R* p = sg + (3 * v + n) * N3 + si;
-        if (D == 0) *p = dv * gx[n];
+        if constexpr (LAST) gq[3 * v + n] = *p + dv * gx[n];
+        else if constexpr (FIRST) *p = dv * gx[n];
         else *p += dv * gx[n];
       }
+    }
+    if constexpr (LAST) {
+      if (A.grad_rho_out) {
+        const int pt = line_pt<N, D>(ln, i);
+#pragma unroll
+        for (int n = 0; n < 3; ++n) A.grad_rho_out[((size_t)e * 3 + n) * N3 + pt] = gq[n];
+      }
+      R q[5], gr0[3], g[kG];
+#pragma unroll
+      for (int v = 0; v < 5; ++v) q[v] = qv[v][i];
+#pragma unroll
+      for (int n = 0; n < 3; ++n) gr0[n] = PERT ? g0[PERT ? n : 0][i] : R(0);
+      const Pt<R> st = point_state<PERT>(q, PERT ? r0[i] : R(0), PERT ? E0l[i] : R(0), A.ph);
+      grad_prim<PERT>(st, gq, gr0, A.ph, g);
+#pragma unroll
+      for (int c = 0; c < kG; ++c) sg[c * N3 + si] = g[c];
     }
   }
 }
 
 // Lifting of every element of the CTA; afterwards the first kG component arrays of the gradient
 // array hold the gradient record (grad rho, trace-free strain, grad p) of the form's variables.
-// `pre` holds the direction-0 prefetch on entry; each later direction's loads are issued before
-// the barrier that precedes it.
+// `pre` holds the first direction's prefetch on entry (direction 1 with kLiftFused, else 0); each
+// later direction's loads are issued before the barrier that precedes it.
 template <int N, bool PERT, class R, int EPB>
 __device__ __forceinline__ void lift_all(const KArgs<R>& A, R* sm, int el, int ln, int e, bool active,
                                          LiftPre<N, R>& pre) {
   using L = Layout<N, PERT, R, EPB>;
   constexpr int N3 = N * N * N;
+  if constexpr (kLiftFused) {
+    // directions 1, 2, then 0, which also forms the record (see lift_dir)
+    if (active) {
+      lift_dir<N, PERT, R, EPB, 1, true, false>(A, sm, el, ln, e, pre);
+      lift_prefetch<N, PERT, R, 2>(A, e, ln, pre);
+    }
+    __syncthreads();
+    if (active) {
+      lift_dir<N, PERT, R, EPB, 2, false, false>(A, sm, el, ln, e, pre);
+      lift_prefetch<N, PERT, R, 0>(A, e, ln, pre);
+    }
+    __syncthreads();
+    if (active) lift_dir<N, PERT, R, EPB, 0, false, true>(A, sm, el, ln, e, pre);
+    if (grad_bulk_store<N>()) fence_async_smem();  // the record may leave by bulk store after the barrier
+    __syncthreads();
+    return;
+  }
   if (active) {
-    lift_dir<N, PERT, R, EPB, 0>(A, sm, el, ln, e, pre);
+    lift_dir<N, PERT, R, EPB, 0, true, false>(A, sm, el, ln, e, pre);
     lift_prefetch<N, PERT, R, 1>(A, e, ln, pre);
   }
   __syncthreads();
   if (active) {
-    lift_dir<N, PERT, R, EPB, 1>(A, sm, el, ln, e, pre);
+    lift_dir<N, PERT, R, EPB, 1, false, false>(A, sm, el, ln, e, pre);
     lift_prefetch<N, PERT, R, 2>(A, e, ln, pre);
   }
   __syncthreads();
-  if (active) lift_dir<N, PERT, R, EPB, 2>(A, sm, el, ln, e, pre);
+  if (active) lift_dir<N, PERT, R, EPB, 2, false, false>(A, sm, el, ln, e, pre);
   __syncthreads();
   if (active) {
     const R* sq = sm + L::oQ + el * L::SQ;
@@ -500,6 +554,7 @@ __device__ __forceinline__ void lift_all(const KArgs<R>& A, R* sm, int el, int l
       for (int c = 0; c < kG; ++c) sg[c * N3 + si] = g[c];
     }
   }
+  if (grad_bulk_store<N>()) fence_async_smem();  // the record may leave by bulk store after the barrier
   __syncthreads();
 }
 
@@ -600,7 +655,7 @@ __global__ void __launch_bounds__(EPB * N * N, sizeof(R) == 4 ? grad_min_blocks<
   __syncthreads();
   LiftPre<N, R> pre;
   stage_elements<N, PERT, R, EPB, false>(A, sm, &bar, ne, [&] {
-    if (active) lift_prefetch<N, PERT, R, 0>(A, e, ln, pre);
+    if (active) lift_prefetch<N, PERT, R, kLiftFused ? 1 : 0>(A, e, ln, pre);
   });
   __syncthreads();
   lift_all<N, PERT, R, EPB>(A, sm, el, ln, e, active, pre);
@@ -615,16 +670,28 @@ __global__ void __launch_bounds__(EPB * N * N, sizeof(R) == 4 ? grad_min_blocks<
         for (int n = 0; n < 3; ++n)
           s3f[d][side][n] = __ldg(A.m.Sf + ((size_t)e * 3 + d) * 3 * (N + 1) * N2 + (n * (N + 1) + side * N) * N2 + ln);
   }
-  if (A.G_out != nullptr) {
-    using L = Layout<N, PERT, R, EPB>;
-    constexpr int N3 = N * N * N;
+  // the gradient record out: one bulk store per element (issued by thread 0, overlapping the viscous
+  // face pass, which only reads shared memory), else a strided copy
+  using L = Layout<N, PERT, R, EPB>;
+  constexpr int N3 = N * N * N;
+  constexpr uint32_t kGBytes = kG * N3 * sizeof(R);
+  const bool g_bulk = grad_bulk_store<N>() && A.G_out != nullptr && kGBytes % 16 == 0 && (L::SG * sizeof(R)) % 16 == 0 &&
+                      ((uintptr_t)A.G_out & 15u) == 0;
+  if (g_bulk) {
+    if (threadIdx.x == 0) {
+      for (int j = 0; j < ne; ++j) bulk_s2g(A.G_out + (size_t)(e0 + j) * kG * N3, sm + L::oG + j * L::SG, kGBytes);
+      bulk_commit();
+    }
+  } else if (A.G_out != nullptr) {
     for (int i = threadIdx.x; i < ne * kG * N3; i += blockDim.x)
       A.G_out[(size_t)e0 * kG * N3 + i] = sm[L::oG + (i / (kG * N3)) * L::SG + i % (kG * N3)];
   }
-  if (!active || A.Tv_out == nullptr) return;
-  face_visc_dir<N, PERT, R, EPB, 0, KR>(A, sm, el, ln, e, s3f[0]);
-  face_visc_dir<N, PERT, R, EPB, 1, KR>(A, sm, el, ln, e, s3f[1]);
-  face_visc_dir<N, PERT, R, EPB, 2, KR>(A, sm, el, ln, e, s3f[2]);
+  if (active && A.Tv_out != nullptr) {
+    face_visc_dir<N, PERT, R, EPB, 0, KR>(A, sm, el, ln, e, s3f[0]);
+    face_visc_dir<N, PERT, R, EPB, 1, KR>(A, sm, el, ln, e, s3f[1]);
+    face_visc_dir<N, PERT, R, EPB, 2, KR>(A, sm, el, ln, e, s3f[2]);
+  }
+  if (g_bulk && threadIdx.x == 0) bulk_wait_read();  // the CTA's shared memory must outlive the reads
 }
 
 // ------------------------------------------------------------------ flux sweep, one direction
@@ -633,7 +700,8 @@ __global__ void __launch_bounds__(EPB * N * N, sizeof(R) == 4 ? grad_min_blocks<
 // the two ends (Rusanov + averaged viscous; walls per Section 5), derivative back to the solution
 // points (Eq. 18), accumulated into the divergence array.
 template <int N, bool PERT, class R, int EPB, int D, bool KR>
-__device__ __forceinline__ void flux_dir(const KArgs<R>& A, R* sm, int el, int ln, int e, const FluxPre<R>& pre) {
+__device__ __forceinline__ void flux_dir(const KArgs<R>& A, R* sm, int el, int ln, int e, const FluxPre<R>& pre,
+                                         const int* snb) {
   using L = Layout<N, PERT, R, EPB, true>;
   constexpr int N2 = N * N, N3 = N * N * N;
   const R* sq = sm + L::oQ + el * L::SQ;
@@ -744,9 +812,20 @@ __device__ __forceinline__ void flux_dir(const KArgs<R>& A, R* sm, int el, int l
       for (int v = 0; v < 5; ++v) Ft[v] = Fi[v] - Fv[v];
     } else {
       const int side = (f == N);
-      const NbFace<R> nb = flux_nb_mode<N>() == 0   ? load_nb<N, PERT, true>(A, e, 2 * D + side, ln)
-                           : flux_nb_mode<N>() == 1 ? load_nb_at<N, PERT, true>(A, pre.nbi[side])
-                                                    : nbc;
+      NbFace<R> nb;
+      if constexpr (flux_nb_mode<N>() == 0) {
+        nb = load_nb<N, PERT, true>(A, e, 2 * D + side, ln);
+      } else if constexpr (flux_nb_mode<N>() == 1) {
+        nb = load_nb_at<N, PERT, true>(A, pre.nbi[side]);
+      } else if constexpr (flux_nb_mode<N>() == 2) {
+        nb = nbc;
+      } else {
+        const int F = 2 * D + side, k = snb[2 * F], c = snb[2 * F + 1];
+        NbIdx x;
+        x.bf = k >= 0 ? k * 6 + (c >> 3) : k;
+        x.tp = k >= 0 ? map_face_pt<N>(ln, c & 7) : 0;
+        nb = load_nb_at<N, PERT, true>(A, x);
+      }
       const R sgn = side ? R(1) : R(-1);
       const R mag = sqrt(s3[0] * s3[0] + s3[1] * s3[1] + s3[2] * s3[2]);
       const R im = qdiv(sgn, mag);
@@ -810,7 +889,7 @@ __device__ __forceinline__ void flux_dir(const KArgs<R>& A, R* sm, int el, int l
 
 // FP32: ask for three resident CTAs per SM (register cap ~168 per thread)
 template <int N, bool PERT, class R, int EPB, int MODE, bool KR>
-__global__ void __launch_bounds__(EPB * N * N, sizeof(R) == 4 ? resid_min_blocks<N>() : 1) k_resid(const KArgs<R> A) {
+__global__ void __launch_bounds__(EPB * N * N, sizeof(R) == 4 ? resid_min_blocks<N, EPB>() : 1) k_resid(const KArgs<R> A) {
   using L = Layout<N, PERT, R, EPB, true>;
   constexpr int N2 = N * N, N3 = N * N * N;
   extern __shared__ __align__(128) unsigned char smem_raw[];
@@ -825,21 +904,27 @@ __global__ void __launch_bounds__(EPB * N * N, sizeof(R) == 4 ? resid_min_blocks
   fill_tables<N, R>(A.ops, sm + L::oTAB);
   __syncthreads();
   FluxPre<R> fp;
+  __shared__ int snb[flux_nb_mode<N>() == 3 ? EPB : 1][12];  // (neighbour, face code) of the 6 faces
   stage_elements<N, PERT, R, EPB, true>(A, sm, &bar, ne, [&] {
     if (active) flux_prefetch<N, PERT, R, 0>(A, e, ln, fp);
+    if (flux_nb_mode<N>() == 3 && active && ln < 6) {
+      snb[el][2 * ln] = __ldg(A.m.nbr + e * 6 + ln);
+      snb[el][2 * ln + 1] = __ldg(A.m.code + e * 6 + ln);
+    }
   });
   __syncthreads();
+  const int* snb_el = snb[flux_nb_mode<N>() == 3 ? el : 0];
   if (active) {
-    flux_dir<N, PERT, R, EPB, 0, KR>(A, sm, el, ln, e, fp);
+    flux_dir<N, PERT, R, EPB, 0, KR>(A, sm, el, ln, e, fp, snb_el);
     flux_prefetch<N, PERT, R, 1>(A, e, ln, fp);
   }
   __syncthreads();
   if (active) {
-    flux_dir<N, PERT, R, EPB, 1, KR>(A, sm, el, ln, e, fp);
+    flux_dir<N, PERT, R, EPB, 1, KR>(A, sm, el, ln, e, fp, snb_el);
     flux_prefetch<N, PERT, R, 2>(A, e, ln, fp);
   }
   __syncthreads();
-  if (active) flux_dir<N, PERT, R, EPB, 2, KR>(A, sm, el, ln, e, fp);
+  if (active) flux_dir<N, PERT, R, EPB, 2, KR>(A, sm, el, ln, e, fp, snb_el);
 
   // Global inputs of the epilogue, all issued before its first store.  The epilogue works point by
   // point, so thread ln takes the points ln + N^2 i (i < N): 16 consecutive threads read 64
