@@ -80,6 +80,15 @@ __host__ __device__ constexpr int grad_min_blocks() { return N <= 5 ? 4 : 2; }
 template <int N>
 __host__ __device__ constexpr bool reg_grad_lines() { return N <= 4; }
 
+// Whether direction 0 of the N = 4 residual sweep visits its end points first, their neighbour data
+// loaded with the staging; and how many flux points ahead the sweep loads the metrics at N = 4 and
+// N = 5 (1 or 2; the other orders, 1: two spill there).
+constexpr bool kEndFirstD0 = false;
+constexpr int kS3AheadN4 = 2;
+constexpr int kS3AheadN5 = 1;
+template <int N>
+__host__ __device__ constexpr int s3_ahead() { return N == 4 ? kS3AheadN4 : N == 5 ? kS3AheadN5 : 1; }
+
 // Lifting order: false = directions 0, 1, 2 and a separate pass that forms the gradient record;
 // true = directions 1, 2, 0 with the record formed in the last sweep.
 constexpr bool kLiftFused = true;
@@ -236,10 +245,19 @@ struct LiftPre {
   NbFace<R> nb[2];
 };
 
+// Members only some orders use (unused members of the struct cost registers at the others).
+template <class R, bool X>
+struct FluxPreExtra {
+  R s3b[3];         // S^D_n at the second flux point the sweep visits (metrics two points ahead)
+  NbFace<R> nb[2];  // the end points' neighbour data (sweeps that visit the end points first)
+};
 template <class R>
-struct FluxPre {
-  R s3[3];       // S^D_n at flux point 1 of the line (the first one the sweep visits)
-  NbIdx nbi[2];  // where the neighbour data of the two end points sit
+struct FluxPreExtra<R, false> {};
+
+template <class R, bool X>
+struct FluxPre : FluxPreExtra<R, X> {
+  R s3[3];       // S^D_n at the first flux point the sweep visits
+  NbIdx nbi[2];  // where the neighbour data of the two end points sit (modes 1, 2)
 };
 
 template <int N, bool PERT, class R, int D>
@@ -265,15 +283,38 @@ __device__ __forceinline__ void lift_prefetch(const KArgs<R>& A, int e, int ln, 
 template <int N>
 __host__ __device__ constexpr int flux_nb_mode() { return N == 4 ? 3 : 2; }
 
-template <int N, bool PERT, class R, int D>
-__device__ __forceinline__ void flux_prefetch(const KArgs<R>& A, int e, int ln, FluxPre<R>& p) {
+// Sweeps whose end points come first: direction 0 at N = 4 (mode 3), whose neighbour data are loaded
+// while the kernel waits for its staged element blocks.
+template <int N, int D>
+__host__ __device__ constexpr bool end_first() {
+  return kEndFirstD0 && D == 0 && flux_nb_mode<N>() == 3;
+}
+
+// The flux point a sweep visits at step it: 1, ..., N, 0, or (end points first) N, 0, 1, ..., N - 1.
+template <int N, bool EF>
+__device__ __forceinline__ int flux_order(int it) {
+  if (EF) return it == 0 ? N : it - 1;
+  return it < N ? it + 1 : 0;
+}
+
+template <int N, bool PERT, class R, int D, bool X>
+__device__ __forceinline__ void flux_prefetch(const KArgs<R>& A, int e, int ln, FluxPre<R, X>& p) {
   constexpr int N2 = N * N;
+  constexpr bool EF = end_first<N, D>();
   const R* Sl = A.m.Sf + ((size_t)e * 3 + D) * 3 * (N + 1) * N2;
 #pragma unroll
-  for (int n = 0; n < 3; ++n) p.s3[n] = __ldg(Sl + (n * (N + 1) + 1) * N2 + ln);  // flux point 1
-  if (flux_nb_mode<N>() >= 1) {
+  for (int n = 0; n < 3; ++n) p.s3[n] = __ldg(Sl + (n * (N + 1) + flux_order<N, EF>(0)) * N2 + ln);
+  if constexpr (s3_ahead<N>() == 2) {
+#pragma unroll
+    for (int n = 0; n < 3; ++n) p.s3b[n] = __ldg(Sl + (n * (N + 1) + flux_order<N, EF>(1)) * N2 + ln);
+  }
+  if (flux_nb_mode<N>() == 1 || flux_nb_mode<N>() == 2) {
     p.nbi[0] = nb_index<N>(A, e, 2 * D, ln);
     p.nbi[1] = nb_index<N>(A, e, 2 * D + 1, ln);
+  }
+  if constexpr (EF) {
+    p.nb[0] = load_nb<N, PERT, true>(A, e, 2 * D, ln);
+    p.nb[1] = load_nb<N, PERT, true>(A, e, 2 * D + 1, ln);
   }
 }
 
@@ -699,8 +740,8 @@ __global__ void __launch_bounds__(EPB * N * N, sizeof(R) == 4 ? grad_min_blocks<
 // Transformed fluxes at the N+1 flux points of the thread's D-line (Eq. 12), common fluxes at
 // the two ends (Rusanov + averaged viscous; walls per Section 5), derivative back to the solution
 // points (Eq. 18), accumulated into the divergence array.
-template <int N, bool PERT, class R, int EPB, int D, bool KR>
-__device__ __forceinline__ void flux_dir(const KArgs<R>& A, R* sm, int el, int ln, int e, const FluxPre<R>& pre,
+template <int N, bool PERT, class R, int EPB, int D, bool KR, bool X>
+__device__ __forceinline__ void flux_dir(const KArgs<R>& A, R* sm, int el, int ln, int e, const FluxPre<R, X>& pre,
                                          const int* snb) {
   using L = Layout<N, PERT, R, EPB, true>;
   constexpr int N2 = N * N, N3 = N * N * N;
@@ -739,15 +780,30 @@ __device__ __forceinline__ void flux_dir(const KArgs<R>& A, R* sm, int el, int l
   // one rolled loop over the flux points keeps a single copy of the flux code per direction
   // Flux points in the order 1, ..., N, 0, so that the neighbour data (prefetched) are first needed
   // after the interior points; S^D at the next flux point is loaded one iteration ahead.
+  constexpr bool EF = end_first<N, D>();
+  constexpr int AH = s3_ahead<N>();
   R s3n[3] = {pre.s3[0], pre.s3[1], pre.s3[2]};
+  R s3nn[AH == 2 ? 3 : 1];
+  if constexpr (AH == 2) {
+#pragma unroll
+    for (int n = 0; n < 3; ++n) s3nn[n] = pre.s3b[n];
+  }
   NbFace<R> nbn;  // mode 2: the next end point's neighbour data
   nbn.kind = -1;
 #pragma unroll 1
   for (int it = 0; it <= N; ++it) {
-    const int f = it < N ? it + 1 : 0;
+    const int f = flux_order<N, EF>(it);
     R s3[3] = {s3n[0], s3n[1], s3n[2]};
-    if (it < N) {
-      const int fn = it + 1 < N ? it + 2 : 0;
+    if constexpr (AH == 2) {
+#pragma unroll
+      for (int n = 0; n < 3; ++n) s3n[n] = s3nn[n];
+      if (it + 2 <= N) {
+        const int fnn = flux_order<N, EF>(it + 2);
+#pragma unroll
+        for (int n = 0; n < 3; ++n) s3nn[n] = __ldg(Sl + (n * (N + 1) + fnn) * N2 + ln);
+      }
+    } else if (it < N) {
+      const int fn = flux_order<N, EF>(it + 1);
 #pragma unroll
       for (int n = 0; n < 3; ++n) s3n[n] = __ldg(Sl + (n * (N + 1) + fn) * N2 + ln);
     }
@@ -813,7 +869,9 @@ __device__ __forceinline__ void flux_dir(const KArgs<R>& A, R* sm, int el, int l
     } else {
       const int side = (f == N);
       NbFace<R> nb;
-      if constexpr (flux_nb_mode<N>() == 0) {
+      if constexpr (EF) {
+        nb = pre.nb[side];
+      } else if constexpr (flux_nb_mode<N>() == 0) {
         nb = load_nb<N, PERT, true>(A, e, 2 * D + side, ln);
       } else if constexpr (flux_nb_mode<N>() == 1) {
         nb = load_nb_at<N, PERT, true>(A, pre.nbi[side]);
@@ -903,7 +961,7 @@ __global__ void __launch_bounds__(EPB * N * N, sizeof(R) == 4 ? resid_min_blocks
   if (threadIdx.x == 0) mbar_init(&bar);
   fill_tables<N, R>(A.ops, sm + L::oTAB);
   __syncthreads();
-  FluxPre<R> fp;
+  FluxPre<R, (N == 4 && kEndFirstD0) || s3_ahead<N>() == 2> fp;
   __shared__ int snb[flux_nb_mode<N>() == 3 ? EPB : 1][12];  // (neighbour, face code) of the 6 faces
   stage_elements<N, PERT, R, EPB, true>(A, sm, &bar, ne, [&] {
     if (active) flux_prefetch<N, PERT, R, 0>(A, e, ln, fp);
