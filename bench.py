@@ -67,17 +67,22 @@ def job_rate(world: int, units_per_rank: float, seconds: float) -> float:
 
 def kernel_sources_digest() -> str:
     """SHA-256 of the residual kernels' sources (the stepping kernels, their headers and the build
-    script with its per-source compiler options): the DRAM counters in profiles/traffic.json are
-    reported only for the sources they were taken on."""
+    script with its per-source compiler options), comments and blank lines left out: the DRAM
+    counters in profiles/traffic.json are reported only for the code they were taken on."""
     import hashlib
+    import re
 
     csrc = os.path.join(ROOT, "paper_1503_00834_gb300", "csrc")
     names = ["internal.h", "sd_device.cuh", "sd_kernels.cuh", "kern_inst.cuh"] + [f"kern_p{p}.cu" for p in (2, 3, 4, 5)]
     names.append(os.path.join("..", "build.py"))
     h = hashlib.sha256()
     for n in names:
-        with open(os.path.join(csrc, n), "rb") as f:
-            h.update(n.encode() + b"\0" + f.read())
+        with open(os.path.join(csrc, n)) as f:
+            text = f.read()
+        # drop C++ line comments (none of these files has "//" inside a string) and Python comments
+        pat = r"#.*$" if n.endswith(".py") else r"//.*$"
+        code = "\n".join(ln.rstrip() for ln in re.sub(pat, "", text, flags=re.M).splitlines() if ln.strip())
+        h.update(n.encode() + b"\0" + code.encode())
     return h.hexdigest()
 
 

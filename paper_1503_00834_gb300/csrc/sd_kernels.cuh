@@ -67,22 +67,30 @@ __device__ __forceinline__ int line_sidx(int ln, int s) {
 // compiler (register cap).
 constexpr bool kResidBgShared = true;
 constexpr int kResidMinBlocksF32 = 3;
+// Resident lifting CTAs asked for at N = 5 (five-element CTAs: three fit the shared memory; with
+// 168 registers a thread the lifting spills 28 bytes instead of 324 at the 128 of four CTAs).
+constexpr int kGradMinBlocksN5 = 3;
+// Whether the xi-line sweeps at N = 4 (FP32) read a line of the gradient record as one 16-byte
+// shared-memory load per component (the swizzled layout keeps a xi-line's 4 points contiguous).
+constexpr bool kVecGradLoad = true;
+
 // Per order, from timings of every combination on the 786,432-element p = 4 and the 98,304-element
 // p = 5 shells: the resident CTAs asked of the compiler for the residual and the lifting kernel, and
 // whether the flux sweep holds the line's gradient record in registers (else it reads it from
 // shared memory per flux point).  N = 6 runs two CTAs of four elements per SM (shared memory) and
-// does best with the registers that allows; N = 5 keeps the N <= 4 requests, with the gradient lines
-// in shared memory.
+// does best with the registers that allows; N = 5 asks for three CTAs of each kernel, with the
+// gradient lines in shared memory.
 template <int N, int EPB>
 __host__ __device__ constexpr int resid_min_blocks() { return N <= 5 ? kResidMinBlocksF32 : 2; }
 template <int N>
-__host__ __device__ constexpr int grad_min_blocks() { return N <= 5 ? 4 : 2; }
+__host__ __device__ constexpr int grad_min_blocks() { return N <= 4 ? 4 : N == 5 ? kGradMinBlocksN5 : 2; }
 template <int N>
 __host__ __device__ constexpr bool reg_grad_lines() { return N <= 4; }
 
 // Whether direction 0 of the N = 4 residual sweep visits its end points first, their neighbour data
-// loaded with the staging; and how many flux points ahead the sweep loads the metrics at N = 4 and
-// N = 5 (1 or 2; the other orders, 1: two spill there).
+// loaded with the staging (3 % slower: off); and how many flux points ahead the sweep loads the
+// metrics at N = 4 and N = 5 (1 or 2: two is 1.4 % faster at N = 4, 0.6 % slower at N = 5; the
+// other orders, 1: two spill there).
 constexpr bool kEndFirstD0 = false;
 constexpr int kS3AheadN4 = 2;
 constexpr int kS3AheadN5 = 1;
@@ -151,6 +159,30 @@ __device__ __forceinline__ void load_line_lin(const R* __restrict__ base, int ln
   } else {
 #pragma unroll
     for (int s = 0; s < N; ++s) out[s] = base[line_pt<N, D>(ln, s)];
+  }
+}
+
+// Load the kG components of the gradient record along line ln of direction D from the shared array.
+template <int N, int D, class R>
+__device__ __forceinline__ void load_grad_lines(const R* sg, int ln, R (&gv)[kG][N]) {
+  constexpr int N3 = N * N * N;
+  if constexpr (D == 0 && N == 4 && sizeof(R) == 4 && kVecGradLoad) {
+    const int s0 = line_sidx<N, 0, R>(ln, 0);
+#pragma unroll
+    for (int c = 0; c < kG; ++c) {
+      const float4 v = *reinterpret_cast<const float4*>(sg + c * N3 + s0);
+      gv[c][0] = v.x;
+      gv[c][1] = v.y;
+      gv[c][2] = v.z;
+      gv[c][3] = v.w;
+    }
+  } else {
+#pragma unroll
+    for (int s = 0; s < N; ++s) {
+      const int si = line_sidx<N, D, R>(ln, s);
+#pragma unroll
+      for (int c = 0; c < kG; ++c) gv[c][s] = sg[c * N3 + si];
+    }
   }
 }
 
@@ -622,12 +654,7 @@ __device__ __forceinline__ void face_visc_dir(const KArgs<R>& A, const R* sm, in
   R qv[5][N], gv[kG][N], r0[N], E0l[N], g0[3][N];
 #pragma unroll
   for (int v = 0; v < 5; ++v) load_line_lin<N, D>(sq + v * N3, ln, qv[v]);
-#pragma unroll
-  for (int s = 0; s < N; ++s) {
-    const int si = line_sidx<N, D, R>(ln, s);
-#pragma unroll
-    for (int c = 0; c < kG; ++c) gv[c][s] = sg[c * N3 + si];
-  }
+  load_grad_lines<N, D>(sg, ln, gv);
   if (PERT) {
     load_line_lin<N, D>(sbg, ln, r0);
     load_line_lin<N, D>(sbg + N3, ln, E0l);
@@ -759,12 +786,7 @@ __device__ __forceinline__ void flux_dir(const KArgs<R>& A, R* sm, int el, int l
 #pragma unroll
   for (int v = 0; v < 5; ++v) load_line_lin<N, D>(sq + v * N3, ln, qv[v]);
   if constexpr (kRegGrad) {
-#pragma unroll
-    for (int s = 0; s < N; ++s) {
-      const int si = line_sidx<N, D, R>(ln, s);
-#pragma unroll
-      for (int c = 0; c < kG; ++c) gv[c][s] = sg[c * N3 + si];
-    }
+    load_grad_lines<N, D>(sg, ln, gv);
   }
   // the background line is read from shared memory per flux point (register budget)
   const R* Sl = A.m.Sf + ((size_t)e * 3 + D) * 3 * (N + 1) * N2;
