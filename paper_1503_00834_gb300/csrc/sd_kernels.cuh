@@ -310,10 +310,10 @@ __device__ __forceinline__ void lift_prefetch(const KArgs<R>& A, int e, int ln, 
 // the end point; 1 = index (neighbour, face, orientation) loaded with the sweep's first metrics, data
 // at the end point; 2 = as 1, and the data of each end point issued one flux point ahead; 3 = the
 // element's six (neighbour, face code) pairs staged in shared memory with the state, data loaded at
-// the end point.  Timed per order: 2 is fastest for N = 3, 5, 6; at N = 4 the registers it holds
-// through the sweep spill.
+// the end point.  Timed per order: 3 is fastest at N = 3, 4, 6 (2 spills at N = 4 and is 2 % slower
+// at N = 3, 6); 2 is 0.9 % faster at N = 5.
 template <int N>
-__host__ __device__ constexpr int flux_nb_mode() { return N == 4 ? 3 : 2; }
+__host__ __device__ constexpr int flux_nb_mode() { return (N == 4 || N == 3 || N == 6) ? 3 : 2; }
 
 // Sweeps whose end points come first: direction 0 at N = 4 (mode 3), whose neighbour data are loaded
 // while the kernel waits for its staged element blocks.
