@@ -162,21 +162,48 @@ class ClockSampler:
                 "reasons": sorted(reasons), "samples": len(sm)}
 
 
-def run_reference(args, cfg):
-    """The FP64 CPU oracle on a bounded sample of the workload (residual + stage update)."""
+def cpu_model() -> str:
+    """The host CPU's model name (lscpu, else /proc/cpuinfo) and architecture."""
+    import platform
+
+    name = None
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for ln in out.splitlines():
+            if ln.strip().lower().startswith("model name"):
+                name = ln.split(":", 1)[1].strip()
+                break
+    except Exception:
+        pass
+    if not name:
+        try:
+            with open("/proc/cpuinfo") as f:
+                for ln in f:
+                    if ln.lower().startswith(("model name", "cpu part")):
+                        name = ln.split(":", 1)[1].strip()
+                        break
+        except OSError:
+            pass
+    return f"{name or platform.processor() or 'unknown'} ({platform.machine()})"
+
+
+def _reference_sample(cfg_name: str, e0: int, n_sample: int):
+    """The oracle's one-stage update (residual + stage combination) of elements [e0, e0 + n_sample) of
+    a workload, with the seeded initial state on their two-face-hop patch."""
     import numpy as np
 
-    from chorus_inputs import cubed_sphere_hex20
+    from chorus_inputs import CONFIGS, BATCH_64, cubed_sphere_hex20
     from oracle.physics import Physics
     from oracle.residual import Discretization, residual
     from oracle import state as ostate
 
+    cfg = CONFIGS.get(cfg_name) or next(c for c in BATCH_64.shells() if c.name == cfg_name)
     xyz, h20 = cubed_sphere_hex20(cfg.n, cfg.n_r, cfg.r_inner, cfg.r_outer)
     disc = Discretization(xyz, h20, cfg.p, cfg.r_inner, cfg.r_outer)
     ph = Physics.from_params(cfg.phys, cfg.r_inner, cfg.r_outer)
     N = cfg.p + 1
-    n_sample = min(disc.n_elem, args.ref_elems)
-    elems = np.arange(n_sample)
+    e0 = min(e0, max(0, disc.n_elem - n_sample))
+    elems = np.arange(e0, min(disc.n_elem, e0 + n_sample))
     patch = disc.conn.closure(disc.conn.closure(elems))
     Q = np.zeros((disc.n_elem, 5, N, N, N))
     Q[patch] = ostate.initial_state(ph, disc.geometry(patch)["x"], cfg.seed, cfg.entropy_amp, elems=patch)
@@ -186,16 +213,85 @@ def run_reference(args, cfg):
         R = residual(disc, ph, Q, elems)
         return Q[elems] + dt * R
 
-    for _ in range(max(0, args.warmup)):
+    return one_stage, len(elems) * N ** 3, int(elems[0]), len(elems)
+
+
+def _timed_stages(one_stage, warmup: int, steps, seconds):
+    """Run warm-up stages, then `steps` timed stages (or stages until `seconds` have passed)."""
+    for _ in range(max(0, warmup)):
         one_stage()
     times = []
-    for _ in range(args.steps):
+    t_start = time.perf_counter()
+    while True:
         t0 = time.perf_counter()
         one_stage()
         times.append(time.perf_counter() - t0)
-    units = n_sample * N ** 3
-    value = units * len(times) / sum(times)
-    return value, times, n_sample
+        if steps is not None and len(times) >= steps:
+            break
+        if steps is None and time.perf_counter() - t_start >= seconds:
+            break
+    return times
+
+
+def _reference_worker(cfg_name, e0, n_sample, warmup, steps, seconds, barrier, queue):
+    for var in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS"):
+        os.environ[var] = "1"
+    try:
+        one_stage, units, first, n = _reference_sample(cfg_name, e0, n_sample)
+        barrier.wait(timeout=600)
+        times = _timed_stages(one_stage, warmup, steps, seconds)
+        queue.put((units, times, first, n))
+    except Exception as exc:  # reported by the parent
+        try:
+            barrier.abort()
+        except Exception:
+            pass
+        queue.put(repr(exc))
+
+
+def run_reference(cfg_name: str, n_workers: int, n_sample: int, warmup: int, steps=None, seconds=None):
+    """The plain FP64 oracle (numpy, one thread per process) timed on `n_workers` host cores, each
+    worker on its own block of n_sample elements of the workload, started together.  Returns
+    (DOF-stage/s over all workers, per-step seconds of the slowest worker, description)."""
+    if n_workers <= 1:
+        one_stage, units, first, n = _reference_sample(cfg_name, 0, n_sample)
+        times = _timed_stages(one_stage, warmup, steps, seconds)
+        desc = (f"{len(times)} x (residual + stage update) on elements {first}..{first + n - 1} of {cfg_name} "
+                f"(numpy FP64, one process, one thread), {sum(times):.2f} s")
+        return units * len(times) / sum(times), times, desc
+    import multiprocessing as mp
+
+    ctx = mp.get_context("spawn")  # never fork a process that may hold a CUDA context
+    barrier, queue = ctx.Barrier(n_workers), ctx.Queue()
+    procs = [ctx.Process(target=_reference_worker,
+                         args=(cfg_name, w * n_sample, n_sample, warmup, steps, seconds, barrier, queue))
+             for w in range(n_workers)]
+    for pr in procs:
+        pr.start()
+    res = [queue.get(timeout=1200) for _ in procs]
+    for pr in procs:
+        pr.join(timeout=60)
+    bad = [r for r in res if isinstance(r, str)]
+    if bad:
+        raise RuntimeError(f"reference worker failed: {bad[0]}")
+    units = sum(u * len(t) for u, t, _, _ in res)
+    slowest = max(res, key=lambda r: sum(r[1]))[1]
+    span = max(sum(t) for _, t, _, _ in res)
+    n_el = sum(n for _, _, _, n in res)
+    desc = (f"{n_workers} processes (one thread each) started together, each timing (residual + stage update) "
+            f"on its own {n_sample}-element block of {cfg_name} ({n_el} elements in all; numpy FP64), "
+            f"{span:.2f} s")
+    return units / span, slowest, desc
+
+
+def cpu_baseline(cfg_name: str, n_sample: int, seconds: float) -> dict:
+    """The oracle on the host cores: one core and all cores, about `seconds` of timed work each."""
+    one, _, desc1 = run_reference(cfg_name, 1, n_sample, 1, seconds=seconds)
+    cores = os.cpu_count() or 1
+    allv, _, desc_all = run_reference(cfg_name, cores, n_sample, 1, seconds=seconds) if cores > 1 else (one, None,
+                                                                                                        desc1)
+    return {"value": allv, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": desc_all,
+            "one_core": {"value": one, "cores": 1, "sample": desc1}, "nproc": cores, "cpu_model": cpu_model()}
 
 
 def run_batch(args, rank, world, local):
@@ -261,18 +357,8 @@ def run_batch(args, rank, world, local):
     state_bytes = Q.numel() * Q.element_size()
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        class _A:
-            pass
-
-        a = _A()
-        a.ref_elems, a.warmup, a.steps = args.ref_elems, 1, 1
         cfg0 = next(c for c in sh.cfgs if c.p == 3)
-        v, times, n_sample = run_reference(a, cfg0)
-        a.steps = max(1, int(args.cpu_seconds / max(times[0], 1e-3)))
-        v, times, n_sample = run_reference(a, cfg0)
-        cpu = {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle",
-               "sample": f"{len(times)} x (residual + stage update) on elements 0..{n_sample - 1} of batch shell "
-                         f"{cfg0.name} (p=3; numpy FP64, single thread), {sum(times):.1f} s"}
+        cpu = cpu_baseline(cfg0.name, args.ref_elems, args.cpu_seconds)
     if rank == 0:
         from collections import Counter
 
@@ -300,6 +386,27 @@ def run_batch(args, rank, world, local):
         torch.distributed.destroy_process_group()
 
 
+def stage_roofline(alg_bytes_per_dof: float, n_dof: int, stage_ms: float, peak: float, peak_kind: str,
+                   kernels: dict, traffic: dict) -> dict:
+    """The roofline of the whole RK stage (every kernel of the residual and the update): algorithmic
+    bytes of one stage over its measured time, against the measured HBM copy bandwidth; per kernel
+    its time, measured DRAM bytes (ncu, when taken on these sources) and their rate."""
+    achieved = alg_bytes_per_dof * n_dof / (stage_ms / 1e3) / 1e9
+    tr_stage = None
+    if traffic and all(traffic.get(k) is not None for k in ("k_grad", "k_resid")):
+        tr_stage = traffic["k_grad"] + traffic["k_resid"]
+    per = {}
+    for name, ms in kernels.items():
+        b = traffic.get(name) if traffic else None
+        per[name] = {"launch_ms": ms, "dram_bytes": b,
+                     "dram_gbs": (b / (ms / 1e3) / 1e9) if (b and ms) else None,
+                     "dram_frac": (b / (ms / 1e3) / 1e9 / peak) if (b and ms) else None}
+    return {"bound": "hbm", "kernel": "whole RK stage (k_grad + k_resid per stage; k_trace once per call)",
+            "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak, "traffic": tr_stage,
+            "peak_kind": peak_kind, "alg_bytes_per_dof_stage": alg_bytes_per_dof, "stage_ms": stage_ms,
+            "kernels": per}
+
+
 def main():
     from chorus_inputs import CONFIGS
 
@@ -319,7 +426,6 @@ def main():
     args = ap.parse_args()
     cfg = CONFIGS[args.config]
     rank, world, local = _dist()
-    N = cfg.p + 1
     if args.workload == "batch_64" and args.impl == "chorus":
         run_batch(args, rank, world, local)
         return
@@ -331,15 +437,15 @@ def main():
             from chorus_inputs import BATCH_64
 
             cfg = next(c for c in BATCH_64.shells() if c.p == 3)
-        value, times, n_sample = run_reference(args, cfg)
+        cores = os.cpu_count() or 1
+        value, times, desc = run_reference(cfg.name, cores, args.ref_elems, args.warmup, steps=args.steps)
         line = {
             "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * statistics.mean(times),
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
             "data": "synthetic", "config": {"workload": cfg.name, "elements": cfg.n_elem, "p": cfg.p},
-            "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
-                             "sample": f"one residual + stage update on elements 0..{n_sample - 1} of {cfg.name} "
-                                       f"per step (numpy, single thread)"},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": desc,
+                             "cpu_model": cpu_model()},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
         }
         print(json.dumps(line))
@@ -352,7 +458,7 @@ def main():
         import torch.distributed as dist
 
         dist.init_process_group("nccl")
-    from paper_1503_00834_gb300 import FP32_PERT, FP64, Shell, build as _build
+    from paper_1503_00834_gb300 import FP32_PERT, FP64, Shell, build as _build, native
 
     _build.build()
     prec = FP32_PERT if args.prec == "fp32" else FP64
@@ -366,10 +472,26 @@ def main():
     mesh.prepare(sh.params)
     mesh.state_init(sh.params, cfg.seed, cfg.entropy_amp, prec, Q)
     n_dof = cfg.n_dof
+    # measured arithmetic peaks of this GPU (the FP64 path is bound by its FP64 units)
+    fma = {"fp64_tflops": native.fma_rate(FP64) / 1e12, "fp32_tflops": native.fma_rate(FP32_PERT) / 1e12}
 
     def barrier():
         if world > 1:
             torch.distributed.barrier()
+
+    def timed_steps(prec_, Q_, ws_, n_steps):
+        """n_steps timed SSP-RK3 steps with per-kernel event timing; (ms, kernel ms per launch)."""
+        mesh.timing_enable(True)
+        mesh.timing_read()  # clear
+        ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        ev0.record(stream)
+        mesh.rk_step(sh.params, prec_, Q_, ws_, sh.dt, n_steps)
+        ev1.record(stream)
+        torch.cuda.synchronize()
+        kms, kcnt = mesh.timing_read()
+        mesh.timing_enable(False)
+        per = {nm: kms[c] / max(1, kcnt[c]) for c, nm in enumerate(("k_trace", "k_grad", "k_resid"))}
+        return ev0.elapsed_time(ev1), per, sum(kcnt)
 
     # ---- warm-up, then K timed steps (inputs far larger than L2: state 425 MB FP32)
     mesh.rk_step(sh.params, prec, Q, ws, sh.dt, max(3, args.warmup))
@@ -378,80 +500,58 @@ def main():
     torch.cuda.synchronize()
     clk = ClockSampler(local)
     clk.start()
-    mesh.timing_enable(True)
-    mesh.timing_read()  # clear
-    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    ev0.record(stream)
-    mesh.rk_step(sh.params, prec, Q, ws, sh.dt, args.steps)
-    ev1.record(stream)
-    torch.cuda.synchronize()
+    ms_local, kper, launches = timed_steps(prec, Q, ws, args.steps)
     barrier()
     torch.cuda.synchronize()
     clocks = clk.stop()
-    kms, kcnt = mesh.timing_read()
-    mesh.timing_enable(False)
-    ms = max_over_ranks(ev0.elapsed_time(ev1), world)
+    ms = max_over_ranks(ms_local, world)
     stages = 3 * args.steps
     value = job_rate(world, n_dof * stages, ms / 1e3)
     mesh.check()
 
-    # ---- dominant kernel roofline (residual + stage update kernel)
-    names = ["k_trace", "k_grad", "k_resid"]
-    dom = max(range(3), key=lambda c: kms[c])
-    per_launch_ms = kms[dom] / max(1, kcnt[dom])
+    # ---- roofline of the whole stage
     alg = (ALG_BYTES_PER_DOF_STAGE if prec == FP32_PERT else ALG_BYTES_PER_DOF_STAGE_FP64)[cfg.p]
     peak, peak_kind = _peaks()
-    achieved = alg * n_dof / (per_launch_ms / 1e3) / 1e9
-    traffic = lookup_traffic(os.path.join(ROOT, "profiles", "traffic.json"), names[dom], cfg.name, args.prec)
+    tpath = os.path.join(ROOT, "profiles", "traffic.json")
+    traffic = {k: lookup_traffic(tpath, k, cfg.name, args.prec) for k in ("k_grad", "k_resid")}
+    roof = stage_roofline(alg, n_dof, ms / stages, peak, peak_kind, kper, traffic)
 
-    # ---- FP64 GPU path on the same workload (the metric compares both)
-    fp64_value = None
+    # ---- FP64 GPU path on the same workload (the metric compares both), with its FP64-unit roofline
+    fp64 = None
     if prec == FP32_PERT and args.fp64_steps > 0:
         Q64 = torch.empty(shape, dtype=torch.float64, device="cuda")
         ws64 = torch.empty(mesh.workspace_bytes(FP64), dtype=torch.uint8, device="cuda")
         mesh.state_init(sh.params, cfg.seed, cfg.entropy_amp, FP64, Q64)
         mesh.rk_step(sh.params, FP64, Q64, ws64, sh.dt, 1)
-        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        e0.record(stream)
-        mesh.rk_step(sh.params, FP64, Q64, ws64, sh.dt, args.fp64_steps)
-        e1.record(stream)
         torch.cuda.synchronize()
-        fp64_value = world * n_dof * 3 * args.fp64_steps / (e0.elapsed_time(e1) / 1e3)
+        ms64, kper64, _ = timed_steps(FP64, Q64, ws64, args.fp64_steps)
+        v64 = world * n_dof * 3 * args.fp64_steps / (ms64 / 1e3)
+        fpath = os.path.join(ROOT, "profiles", "fp64_flops.json")
+        fl = lookup_traffic(fpath, "stage", cfg.name, "fp64")  # FP64 flops per DOF-stage (ncu instruction counts)
+        fp64 = {"value": v64, "unit": UNIT, "ms_per_step": ms64 / args.fp64_steps,
+                "kernels_ms_per_launch": kper64,
+                "roofline": {"bound": "alu", "unit": "TFLOP/s", "peak": fma["fp64_tflops"], "peak_kind": "measured",
+                             "flops_per_dof_stage": fl,
+                             "achieved": (fl * v64 / 1e12) if fl else None,
+                             "frac": (fl * v64 / 1e12 / fma["fp64_tflops"]) if fl else None}}
         del Q64, ws64
 
-    # ---- end to end through the public API with host buffers: H2D state, K steps, D2H state
+    # ---- end to end through the public API with host buffers: each step copies the state in from
+    # pinned host memory, steps, and copies it back (chorus_rk_step_host)
     host = torch.empty(shape, dtype=tdt, pin_memory=True)
     host.copy_(Q)
-    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     torch.cuda.synchronize()
-    e0.record(stream)
+    t0 = time.perf_counter()
     for _ in range(args.e2e_steps):
-        Q.copy_(host, non_blocking=True)
-        mesh.rk_step(sh.params, prec, Q, ws, sh.dt, 1)
-        host.copy_(Q, non_blocking=True)
-    e1.record(stream)
-    torch.cuda.synchronize()
-    e2e_ms = e0.elapsed_time(e1)
-    e2e_value = world * n_dof * 3 * args.e2e_steps / (e2e_ms / 1e3)
+        mesh.rk_step_host(sh.params, prec, host, Q, ws, sh.dt, 1)
+    e2e_s = time.perf_counter() - t0
+    e2e_value = world * n_dof * 3 * args.e2e_steps / e2e_s
     state_bytes = Q.numel() * Q.element_size()
 
     # ---- CPU baseline: the oracle on a bounded sample, rank 0 at N=1 only
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        class _A:
-            pass
-
-        a = _A()
-        a.ref_elems, a.warmup = args.ref_elems, 1
-        a.steps = 1
-        t0 = time.perf_counter()
-        v, times, n_sample = run_reference(a, cfg)
-        per = times[0]
-        a.steps = max(1, int(args.cpu_seconds / max(per, 1e-3)))
-        v, times, n_sample = run_reference(a, cfg)
-        cpu = {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle",
-               "sample": f"{len(times)} x (residual + stage update) on elements 0..{n_sample - 1} of {cfg.name} "
-                         f"(numpy FP64, single thread), {sum(times):.1f} s"}
+        cpu = cpu_baseline(cfg.name, args.ref_elems, args.cpu_seconds)
 
     if rank == 0:
         line = {
@@ -464,17 +564,14 @@ def main():
                        "step": "one SSP-RK3 step = 3 residual + stage-update passes",
                        "l2": "inputs larger than L2 (state %.0f MB)" % (state_bytes / 1e6),
                        "parallelism": f"replicas x{world}"},
-            "fp64_gpu_value": fp64_value,
-            "roofline": {"bound": "hbm", "kernel": names[dom], "achieved": achieved, "peak": peak, "unit": "GB/s",
-                         "frac": achieved / peak, "traffic": traffic, "peak_kind": peak_kind,
-                         "alg_bytes_per_dof_stage": alg, "launch_ms": per_launch_ms,
-                         "stage_frac": alg * n_dof / (ms / stages / 1e3) / 1e9 / peak},
-            "kernel_ms": {names[c]: kms[c] for c in range(3)},
-            "kernel_launches": {names[c]: kcnt[c] for c in range(3)},
-            "gpu_launches": int(sum(kcnt)),
+            "roofline": roof,
+            "fp64_gpu_value": fp64["value"] if fp64 else None,
+            "fp64": fp64,
+            "measured_fma_peaks": fma,
+            "gpu_launches": int(launches),
             "clocks": clocks,
             "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": state_bytes,
-                    "d2h_bytes_per_step": state_bytes},
+                    "d2h_bytes_per_step": state_bytes, "call": "chorus_rk_step_host (host state in and out)"},
             "cpu_baseline": cpu,
         }
         print(json.dumps(line))

@@ -30,7 +30,9 @@
  *  - Errors: arguments are validated before any launch (CHORUS_EINVAL,
  *    CHORUS_EMESH); a CUDA error from a launch or copy returns CHORUS_ECUDA;
  *    a device-side timeout of a bounded wait is reported as CHORUS_ETIMEOUT
- *    by the next call that synchronises (chorus_reduce, chorus_check).
+ *    by the next call that synchronises (chorus_reduce, chorus_check), which
+ *    then clears the flag.  A kernel whose wait ran out writes none of its
+ *    outputs, so check before using a result when timeouts are possible.
  *    No call aborts the process or traps the GPU.
  */
 #ifndef CHORUS_H
@@ -138,6 +140,25 @@ chorus_status chorus_state_init(chorus_mesh mesh, const chorus_params* params, u
 chorus_status chorus_residual(chorus_mesh mesh, const chorus_params* params, chorus_precision prec,
                               const void* Q, void* R, void* workspace, void* stream);
 
+/* The fixed explicit time step of the workloads (the paper states only a CFL condition, Section 7.5):
+ * dt = 0.25 h_min / ((2p + 1) c_max), capped by 0.25 h_min^2 / ((2p + 1)^2 max(nu, kappa)), with
+ * c_max = sqrt(gamma R T_a(r_inner)) the largest sound speed of the polytrope at rest of params
+ * (Eqs. 25-27; T_a peaks at the inner wall).  h / ((2p + 1) c) is the one-dimensional limit of the
+ * degree-p SD operator; elements with comparable edges share it among three directions, hence 0.25.
+ * chorus_stable_dt_rule takes the order and the shortest element edge h_min (host computation, no
+ * GPU); chorus_stable_dt takes them from the mesh (chorus_mesh_info's h_min).  dt: host double.
+ * Bad arguments: CHORUS_EINVAL; a non-finite or non-positive result: CHORUS_ENAN. */
+chorus_status chorus_stable_dt_rule(int p, double h_min, double r_inner, double r_outer,
+                                    const chorus_params* params, double* dt);
+chorus_status chorus_stable_dt(chorus_mesh mesh, const chorus_params* params, double* dt);
+
+/* Measured fused multiply-add rate of the current GPU, for rooflines (a measurement helper with no
+ * counterpart in the paper): 8 independent FMA chains per thread on 8 CTAs of 256 threads per SM,
+ * timed with CUDA events on `stream` over a launch sized to about 20 ms, 2 flops per FMA.
+ * prec CHORUS_FP64: double; CHORUS_FP32_PERT: float.  flops_per_s: host double.  Allocates and frees
+ * a small output buffer (stream-ordered) and synchronises the stream. */
+chorus_status chorus_fma_rate(int prec, void* stream, double* flops_per_s);
+
 /* Bytes of device scratch needed by chorus_residual and chorus_rk_step. */
 size_t chorus_rk_workspace_bytes(chorus_mesh mesh, chorus_precision prec);
 
@@ -145,6 +166,14 @@ size_t chorus_rk_workspace_bytes(chorus_mesh mesh, chorus_precision prec);
  * u1 = u + dt L(u); u2 = 3/4 u + 1/4 (u1 + dt L(u1)); u^{n+1} = 1/3 u + 2/3 (u2 + dt L(u2))). */
 chorus_status chorus_rk_step(chorus_mesh mesh, const chorus_params* params, chorus_precision prec,
                              void* Q, void* workspace, double dt, int64_t n_steps, void* stream);
+
+/* chorus_rk_step on a state held in host memory: copies Q_host (host, the state layout, pinned for
+ * full copy bandwidth) to Q_dev (device, caller-owned, same size), takes n_steps SSP-RK3 steps there,
+ * copies the result back into Q_host and synchronises the stream.  workspace as for chorus_rk_step.
+ * This is the end-to-end form of a step for callers whose state lives on the host. */
+chorus_status chorus_rk_step_host(chorus_mesh mesh, const chorus_params* params, chorus_precision prec,
+                                  void* Q_host, void* Q_dev, void* workspace, double dt, int64_t n_steps,
+                                  void* stream);
 
 /* n_steps steps of an explicit SSP scheme, in place on Q.  scheme 0: the SSP-RK3 of
  * chorus_rk_step; scheme 1: the five-stage fourth-order SSP-RK(5,4) of Spiteri and Ruuth that the
@@ -264,7 +293,12 @@ chorus_status chorus_timing_read(chorus_mesh mesh, void* stream, double* ms, int
  *  - Sharing: all calls share the one array and it keeps the previous call's contents (every call
  *    overwrites all it reads, nothing needs to start at zero).  Calls that overlap on the GPU (other
  *    streams, other threads) race on it and must be serialised by the caller.
- *  - FP32_PERT needs chorus_prepare with the same params first, as chorus_residual does. */
+ *  - FP32_PERT needs chorus_prepare with the same params first, as chorus_residual does.
+ *  - An attached closure (chorus_closure_attach) is added as chorus_residual adds it; its output
+ *    buffer was allocated by the attach call.  FP64 with a closure needs chorus_prepare.
+ *  - A radial kappa_r(r) (kappa_r1 or kappa_r2 non-zero) needs its flux-point table, which
+ *    chorus_prepare (or any call with a workspace) builds for the mesh; without it this call returns
+ *    CHORUS_EINVAL instead of allocating. */
 chorus_status chorus_residual_noalloc(chorus_mesh mesh, const chorus_params* params, chorus_precision prec,
                                       const void* Q, void* R, void* stream);
 
@@ -337,8 +371,18 @@ chorus_status chorus_batch_autotune(chorus_batch batch, float* Q, void* workspac
  * chorus_rk_step / chorus_rk_step_scheme in the FP32 perturbation form. */
 chorus_status chorus_set_well_balanced(chorus_mesh mesh, int enable);
 
-/* Synchronise the stream and report a pending device-side error flag (CHORUS_ETIMEOUT). */
+/* Synchronise the stream and report a pending device-side error flag (CHORUS_ETIMEOUT) of the
+ * mesh's kernels, then clear it. */
 chorus_status chorus_check(chorus_mesh mesh, void* stream);
+
+/* Limit of the bounded device-side waits with which the residual and lifting kernels of this mesh
+ * wait for the bulk copies that stage each element's state, background and gradient blocks in shared
+ * memory: after `polls` polls the wait gives up, the kernel sets the mesh's error flag, waits (with
+ * the default limit) for its copies still in flight and returns without computing or storing
+ * anything; chorus_check then reports CHORUS_ETIMEOUT.  polls < 0 restores the default (2^24 polls
+ * with back-off, about a second); 0 makes every wait give up at once, so the failure path can be
+ * exercised without a fault.  polls >= 2^32 - 1: CHORUS_EINVAL.  Synchronous. */
+chorus_status chorus_set_wait_limit(chorus_mesh mesh, int64_t polls);
 
 const char* chorus_strerror(chorus_status status);
 

@@ -6,7 +6,7 @@ cubed-sphere inputs.
 """
 from __future__ import annotations
 
-from .native import FP32_PERT, FP64, Batch, ChorusError, Mesh, Params, load, max_sound_speed, stable_dt  # noqa: F401
+from .native import FP32_PERT, FP64, Batch, ChorusError, Mesh, Params, load, stable_dt  # noqa: F401
 
 
 class Shell:
@@ -21,8 +21,7 @@ class Shell:
         self.params = Params.from_phys(cfg.phys)
         info = self.mesh.info()
         self.h_min = info["h_min"]
-        ph = cfg.phys
-        self.dt = stable_dt(cfg.p, self.h_min, max_sound_speed(ph, cfg.r_inner, cfg.r_outer), max(ph.nu, ph.kappa))
+        self.dt = self.mesh.stable_dt(self.params)
 
 
 class Shells:
@@ -40,6 +39,5 @@ class Shells:
             shells.append((xyz, h20, c.p, c.seed, c.entropy_amp))
         self.params = Params.from_phys(bcfg.phys)
         self.batch = Batch(shells, bcfg.r_inner, bcfg.r_outer, self.params, stream)
-        ph = bcfg.phys
-        c = max_sound_speed(ph, bcfg.r_inner, bcfg.r_outer)
-        self.dt = min(stable_dt(p, h, c, max(ph.nu, ph.kappa)) for p, h in self.batch.group_h_min.items())
+        self.dt = min(stable_dt(p, h, bcfg.r_inner, bcfg.r_outer, self.params)
+                      for p, h in self.batch.group_h_min.items())

@@ -3,6 +3,7 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <algorithm>
 #include <cmath>
 #include <cstring>
 #include <new>
@@ -318,6 +319,27 @@ __global__ void k_am_update(int64_t n_pts, int N3, R* __restrict__ q, const doub
 
 constexpr int kRedBlocks = 1024;
 
+// Arithmetic-rate probe for rooflines: every thread runs kChains independent FMA chains of `iters`
+// steps (x = x a + b) and stores their sum so that nothing is dead code.
+constexpr int kChains = 8;
+template <class T>
+__global__ void __launch_bounds__(256) k_fma_rate(int iters, T a, T b, T* __restrict__ out) {
+  T x[kChains];
+#pragma unroll
+  for (int j = 0; j < kChains; ++j) x[j] = (T)(threadIdx.x + j);
+#pragma unroll 1
+  for (int it = 0; it < iters; ++it) {
+#pragma unroll
+    for (int k = 0; k < 16; ++k)
+#pragma unroll
+      for (int j = 0; j < kChains; ++j) x[j] = fma(x[j], a, b);
+  }
+  T s = (T)0;
+#pragma unroll
+  for (int j = 0; j < kChains; ++j) s += x[j];
+  out[blockIdx.x * (size_t)blockDim.x + threadIdx.x] = s;
+}
+
 template <class R>
 void fill_ops(const Tables1D& T, OpsArg<R>* o) {
   std::memset(o, 0, sizeof(*o));
@@ -448,8 +470,19 @@ bool same_params(const chorus_params& a, const chorus_params& b) {
 
 inline dim3 grid1(int64_t n, int bs = 256) { return dim3((unsigned)((n + bs - 1) / bs)); }
 
+// Report a pending device-side error flag once: CHORUS_ETIMEOUT if set (then cleared), else OK.
+chorus_status take_flag(chorus_mesh_s* m) {
+  unsigned err = 0;
+  CHK(cudaMemcpy(&err, m->d_err, sizeof(unsigned), cudaMemcpyDeviceToHost));
+  if (err == 0) return CHORUS_OK;
+  CHK(cudaMemset(m->d_err, 0, sizeof(unsigned)));
+  return CHORUS_ETIMEOUT;
+}
+
 // Build (or refresh) the radiative-diffusivity table when the params vary kappa_r with radius.
-chorus_status ensure_kr(chorus_mesh_s* m, const chorus_params& P, cudaStream_t st) {
+// may_alloc false: a missing table is not allocated (CHORUS_EINVAL instead); refreshing an existing
+// one for other coefficients allocates nothing.
+chorus_status ensure_kr(chorus_mesh_s* m, const chorus_params& P, cudaStream_t st, bool may_alloc = true) {
   const bool active = P.kappa_r1 != 0.0 || P.kappa_r2 != 0.0;
   if (!active) {
     m->kr_active = false;
@@ -460,6 +493,7 @@ chorus_status ensure_kr(chorus_mesh_s* m, const chorus_params& P, cudaStream_t s
   if (m->kr_active && m->kr_coef[0] == P.kappa_r && m->kr_coef[1] == P.kappa_r1 && m->kr_coef[2] == P.kappa_r2)
     return CHORUS_OK;
   const int64_t nF = m->E * 3 * (m->N + 1) * m->N * m->N;
+  if (!m->d_kr64 && !may_alloc) return CHORUS_EINVAL;
   if (!m->d_kr64 && (dev_alloc(&m->d_kr64, (size_t)nF) != cudaSuccess || dev_alloc(&m->d_kr32, (size_t)nF) != cudaSuccess))
     return CHORUS_ENOMEM;
   k_kr_table<<<grid1(nF), 256, 0, st>>>(m->E, m->N, m->d_x64, m->ops64, P.kappa_r, P.kappa_r1, P.kappa_r2, m->d_kr64,
@@ -779,6 +813,7 @@ chorus_status chorus_residual(chorus_mesh m, const chorus_params* P, chorus_prec
     }));
     RkCoef<double> rc{};
     if (m->closure) {
+      if (!m->prepared) return CHORUS_EINVAL;  // the network reads q' = Q - Q0
       CHK(mlp_elements_tc(0, m->closure, Q, m->d_Q0, m->closure_buf, m->E, 0, m->d_err, st));
       rc.radd = (const double*)m->closure_buf;
     }
@@ -790,6 +825,8 @@ chorus_status chorus_residual(chorus_mesh m, const chorus_params* P, chorus_prec
   }
   if (prec != CHORUS_FP32_PERT) return CHORUS_EINVAL;
   if (!m->prepared || !same_params(m->prep, *P)) return CHORUS_EINVAL;
+  const chorus_status ks = ensure_kr(m, *P, st);
+  if (ks != CHORUS_OK) return ks;
   const PhysArg<float> ph = phys_arg<float>(*P, m->r_inner, m->r_outer);
   const MeshArg<float> ma = mesh_arg<float>(m);
   Ws<float> w = split_ws<float>(m, workspace);
@@ -875,6 +912,7 @@ chorus_status chorus_rk_step_scheme(chorus_mesh m, const chorus_params* P, choru
   if (n_steps == 0) return CHORUS_OK;
   cudaStream_t st = (cudaStream_t)stream;
   if (prec == CHORUS_FP64) {
+    if (m->closure && !m->prepared) return CHORUS_EINVAL;  // the network reads q' = Q - Q0
     const chorus_status ks = ensure_kr(m, *P, st);
     if (ks != CHORUS_OK) return ks;
     const PhysArg<double> ph = phys_arg<double>(*P, m->r_inner, m->r_outer);
@@ -892,6 +930,8 @@ chorus_status chorus_rk_step_scheme(chorus_mesh m, const chorus_params* P, choru
   }
   if (prec != CHORUS_FP32_PERT) return CHORUS_EINVAL;
   if (!m->prepared || !same_params(m->prep, *P)) return CHORUS_EINVAL;
+  const chorus_status ks = ensure_kr(m, *P, st);
+  if (ks != CHORUS_OK) return ks;
   const PhysArg<float> ph = phys_arg<float>(*P, m->r_inner, m->r_outer);
   const MeshArg<float> ma = mesh_arg<float>(m);
   const BgArg bg = bg_arg(m);
@@ -908,6 +948,19 @@ chorus_status chorus_rk_step_scheme(chorus_mesh m, const chorus_params* P, choru
 chorus_status chorus_rk_step(chorus_mesh m, const chorus_params* P, chorus_precision prec, void* Q, void* workspace,
                              double dt, int64_t n_steps, void* stream) {
   return chorus_rk_step_scheme(m, P, prec, 0, Q, workspace, dt, n_steps, stream);
+}
+
+chorus_status chorus_rk_step_host(chorus_mesh m, const chorus_params* P, chorus_precision prec, void* Q_host,
+                                  void* Q_dev, void* workspace, double dt, int64_t n_steps, void* stream) {
+  if (!m || !Q_host || !Q_dev || (prec != CHORUS_FP64 && prec != CHORUS_FP32_PERT)) return CHORUS_EINVAL;
+  const size_t bytes = (size_t)m->E * 5 * m->N * m->N * m->N * (prec == CHORUS_FP64 ? sizeof(double) : sizeof(float));
+  cudaStream_t st = (cudaStream_t)stream;
+  CHK(cudaMemcpyAsync(Q_dev, Q_host, bytes, cudaMemcpyHostToDevice, st));
+  const chorus_status s = chorus_rk_step_scheme(m, P, prec, 0, Q_dev, workspace, dt, n_steps, stream);
+  if (s != CHORUS_OK) return s;
+  CHK(cudaMemcpyAsync(Q_host, Q_dev, bytes, cudaMemcpyDeviceToHost, st));
+  CHK(cudaStreamSynchronize(st));
+  return CHORUS_OK;
 }
 
 chorus_status chorus_reduce(chorus_mesh m, const chorus_params* P, chorus_precision prec, const void* Q, double* out,
@@ -935,9 +988,7 @@ chorus_status chorus_reduce(chorus_mesh m, const chorus_params* P, chorus_precis
   out[3] = std::sqrt(r[3] * r[3] + r[4] * r[4] + r[5] * r[5]);
   for (int i = 0; i < 4; ++i)
     if (!std::isfinite(out[i])) return CHORUS_ENAN;
-  unsigned err = 0;
-  CHK(cudaMemcpy(&err, m->d_err, sizeof(unsigned), cudaMemcpyDeviceToHost));
-  return err ? CHORUS_ETIMEOUT : CHORUS_OK;
+  return take_flag(m);
 }
 
 chorus_status chorus_am_correct(chorus_mesh m, const chorus_params* P, chorus_precision prec, void* Q,
@@ -1145,9 +1196,79 @@ chorus_status chorus_timing_read(chorus_mesh m, void* stream, double* ms, int64_
 chorus_status chorus_check(chorus_mesh m, void* stream) {
   if (!m) return CHORUS_EINVAL;
   CHK(cudaStreamSynchronize((cudaStream_t)stream));
-  unsigned err = 0;
-  CHK(cudaMemcpy(&err, m->d_err, sizeof(unsigned), cudaMemcpyDeviceToHost));
-  return err ? CHORUS_ETIMEOUT : CHORUS_OK;
+  return take_flag(m);
+}
+
+chorus_status chorus_set_wait_limit(chorus_mesh m, int64_t polls) {
+  if (!m || polls >= (int64_t)0xFFFFFFFFu) return CHORUS_EINVAL;
+  const unsigned v = polls < 0 ? 0u : (unsigned)polls + 1u;  // device encoding: 0 default, k + 1 = k polls
+  CHK(cudaMemcpy(m->d_err + 1, &v, sizeof(v), cudaMemcpyHostToDevice));
+  return CHORUS_OK;
+}
+
+chorus_status chorus_stable_dt_rule(int p, double h_min, double r_inner, double r_outer, const chorus_params* P,
+                                    double* dt) {
+  if (!dt || !params_ok(P) || p < 2 || p > 5 || !(h_min > 0.0) || !(r_inner > 0.0) || !(r_outer > r_inner))
+    return CHORUS_EINVAL;
+  // largest sound speed of the polytrope at rest (Eqs. 25-27): at the inner wall, where chi and T peak
+  const PhysArg<double> ph = phys_arg<double>(*P, r_inner, r_outer);
+  const double T_i = ph.p_c / (P->R_gas * ph.rho_c) * (ph.chi_c + ph.chi_ad / r_inner);
+  const double c_max = std::sqrt(P->gamma * P->R_gas * T_i);
+  const double k = 2.0 * p + 1.0;
+  double d = 0.25 * h_min / (k * c_max);
+  const double diff = std::max(P->nu, P->kappa);
+  if (diff > 0.0) d = std::min(d, 0.25 * h_min * h_min / (k * k * diff));
+  if (!(d > 0.0) || !std::isfinite(d)) return CHORUS_ENAN;
+  *dt = d;
+  return CHORUS_OK;
+}
+
+chorus_status chorus_fma_rate(int prec, void* stream, double* flops_per_s) {
+  if (!flops_per_s || (prec != CHORUS_FP64 && prec != CHORUS_FP32_PERT)) return CHORUS_EINVAL;
+  cudaStream_t st = (cudaStream_t)stream;
+  int dev = 0, sms = 0;
+  CHK(cudaGetDevice(&dev));
+  CHK(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+  const int blocks = sms * 8, threads = 256;
+  const size_t n = (size_t)blocks * threads;
+  void* out = nullptr;
+  CHK(cudaMallocAsync(&out, n * 8, st));
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  cudaError_t ce = cudaEventCreate(&e0);
+  if (ce == cudaSuccess) ce = cudaEventCreate(&e1);
+  auto run = [&](int iters) -> cudaError_t {
+    if (prec == CHORUS_FP64)
+      k_fma_rate<double><<<blocks, threads, 0, st>>>(iters, 0.999999, 1e-7, (double*)out);
+    else
+      k_fma_rate<float><<<blocks, threads, 0, st>>>(iters, 0.9999f, 1e-4f, (float*)out);
+    return cudaGetLastError();
+  };
+  // size the timed launch to about 20 ms from a short one, then time it
+  int iters = 64;
+  float ms = 0.f;
+  for (int pass = 0; pass < 3 && ce == cudaSuccess; ++pass) {
+    ce = cudaEventRecord(e0, st);
+    if (ce == cudaSuccess) ce = run(iters);
+    if (ce == cudaSuccess) ce = cudaEventRecord(e1, st);
+    if (ce == cudaSuccess) ce = cudaEventSynchronize(e1);
+    if (ce == cudaSuccess) ce = cudaEventElapsedTime(&ms, e0, e1);
+    if (ce == cudaSuccess && pass < 2) {
+      const double scale = 20.0 / std::max(ms, 1e-3f);
+      iters = (int)std::min(std::max(iters * scale, 64.0), 1e8);
+    }
+  }
+  if (e0) cudaEventDestroy(e0);
+  if (e1) cudaEventDestroy(e1);
+  cudaFreeAsync(out, st);
+  if (ce != cudaSuccess) return CHORUS_ECUDA;
+  CHK(cudaStreamSynchronize(st));
+  *flops_per_s = 2.0 * kChains * 16.0 * (double)iters * (double)n / (ms * 1e-3);
+  return CHORUS_OK;
+}
+
+chorus_status chorus_stable_dt(chorus_mesh m, const chorus_params* P, double* dt) {
+  if (!m) return CHORUS_EINVAL;
+  return chorus_stable_dt_rule(m->p, m->host.h_min, m->r_inner, m->r_outer, P, dt);
 }
 
 }  // extern "C"
@@ -1197,22 +1318,31 @@ extern "C" chorus_status chorus_residual_noalloc(chorus_mesh m, const chorus_par
   const size_t nT = E * 6 * 5 * N2, nTv = E * 6 * 4 * N2, nG = E * kG * N3;
   if ((nT + nTv + nG) * word > kNoAllocScratchBytes) return CHORUS_EINVAL;  // mesh too large for the scratch
   if (prec == CHORUS_FP32_PERT && (!m->prepared || !same_params(m->prep, *P))) return CHORUS_EINVAL;
+  // the attached closure's output buffer was allocated by chorus_closure_attach; FP64 reads Q0
+  if (m->closure && prec == CHORUS_FP64 && !m->prepared) return CHORUS_EINVAL;
   void* scratch = nullptr;
   chorus_status s = noalloc_scratch(&scratch);
   if (s != CHORUS_OK) return s;
   cudaStream_t st = (cudaStream_t)stream;
+  // a radial kappa_r(r) needs its flux-point table, built (allocated) by chorus_prepare or a call
+  // with a workspace; here a missing table is an error, not an allocation
+  const chorus_status ks = ensure_kr(m, *P, st, false);
+  if (ks != CHORUS_OK) return ks;
   if (prec == CHORUS_FP64) {
-    const chorus_status ks = ensure_kr(m, *P, st);
-    if (ks != CHORUS_OK) return ks;
     const PhysArg<double> ph = phys_arg<double>(*P, m->r_inner, m->r_outer);
     const MeshArg<double> ma = mesh_arg<double>(m);
     double* T = (double*)scratch;
     double* Tv = T + nT;
     double* G = Tv + nTv;
+    RkCoef<double> rc{};
+    if (m->closure) {
+      CHK(mlp_elements_tc(0, m->closure, Q, m->d_Q0, m->closure_buf, m->E, 0, m->d_err, st));
+      rc.radd = (const double*)m->closure_buf;
+    }
     CHK(m->L.trace64(ma, m->ops64, (const double*)Q, T, st));
     CHK(m->L.grad64(ma, m->ops64, ph, (const double*)Q, T, Tv, nullptr, G, m->d_err, st));
-    CHK(m->L.resid64(ma, m->ops64, ph, (const double*)Q, T, Tv, G, (double*)R, nullptr, RkCoef<double>{}, 0.0,
-                     kModeResidual, m->d_err, st));
+    CHK(m->L.resid64(ma, m->ops64, ph, (const double*)Q, T, Tv, G, (double*)R, nullptr, rc, 0.0, kModeResidual,
+                     m->d_err, st));
     return CHORUS_OK;
   }
   const PhysArg<float> ph = phys_arg<float>(*P, m->r_inner, m->r_outer);
@@ -1221,10 +1351,15 @@ extern "C" chorus_status chorus_residual_noalloc(chorus_mesh m, const chorus_par
   float* T = (float*)scratch;
   float* Tv = T + nT;
   float* G = Tv + nTv;
+  RkCoef<float> rc{};
+  if (m->closure) {
+    CHK(mlp_elements_tc(1, m->closure, Q, nullptr, m->closure_buf, m->E, 0, m->d_err, st));
+    rc.radd = (const float*)m->closure_buf;
+  }
   CHK(m->L.trace32(ma, m->ops32, (const float*)Q, T, st));
   CHK(m->L.grad32(ma, m->ops32, ph, bg, (const float*)Q, T, Tv, G, m->d_err, st));
-  CHK(m->L.resid32(ma, m->ops32, ph, bg, (const float*)Q, T, Tv, G, (float*)R, nullptr, RkCoef<float>{}, 0.0f,
-                   kModeResidual, m->d_err, st));
+  CHK(m->L.resid32(ma, m->ops32, ph, bg, (const float*)Q, T, Tv, G, (float*)R, nullptr, rc, 0.0f, kModeResidual,
+                   m->d_err, st));
   return CHORUS_OK;
 }
 

@@ -79,8 +79,8 @@ __device__ __forceinline__ void fence_before() { asm volatile("tcgen05.fence::be
 __device__ __forceinline__ void fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
 __device__ __forceinline__ void fence_async_smem() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
 
-// Bounded wait for the given phase parity; false (and *err set) if the limit ran out.
-__device__ __forceinline__ bool wait_phase(uint64_t* bar, uint32_t parity, unsigned* err) {
+// Bounded poll of the given phase parity: at most 2^24 polls (about a second with the back-off).
+__device__ __forceinline__ bool poll_phase(uint64_t* bar, uint32_t parity) {
   const uint32_t a = saddr(bar);
   for (uint32_t it = 0; it < (1u << 24); ++it) {
     uint32_t ok;
@@ -92,7 +92,15 @@ __device__ __forceinline__ bool wait_phase(uint64_t* bar, uint32_t parity, unsig
     if (ok) return true;
     if (it > 64) __nanosleep(64);
   }
+  return false;
+}
+
+// Bounded wait for the given phase parity; false (and *err set) if the limit ran out, after one more
+// bounded wait for the operation still in flight (the caller then frees its TMEM and returns).
+__device__ __forceinline__ bool wait_phase(uint64_t* bar, uint32_t parity, unsigned* err) {
+  if (poll_phase(bar, parity)) return true;
   if (err) atomicOr(err, 2u);
+  poll_phase(bar, parity);
   return false;
 }
 

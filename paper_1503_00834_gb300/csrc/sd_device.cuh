@@ -52,10 +52,14 @@ __device__ __forceinline__ void bulk_commit() { asm volatile("cp.async.bulk.comm
 __device__ __forceinline__ void bulk_wait_read() { asm volatile("cp.async.bulk.wait_group.read 0;" ::: "memory"); }
 __device__ __forceinline__ void fence_async_smem() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
 
-// Bounded wait on phase 0 of the barrier.  Returns false (and sets *err) if the limit ran out.
-__device__ __forceinline__ bool mbar_wait0(uint64_t* bar, unsigned* err) {
+// Polls of a bounded mbarrier wait when the mesh sets no limit of its own (about a second with the
+// back-off below).
+constexpr uint32_t kDefaultWaitPolls = 1u << 24;
+
+// Bounded wait on phase 0 of the barrier: at most `polls` polls.  Returns false if they ran out.
+__device__ __forceinline__ bool mbar_try0(uint64_t* bar, uint32_t polls) {
   const uint32_t a = smem_addr(bar);
-  for (uint32_t it = 0; it < (1u << 24); ++it) {
+  for (uint32_t it = 0; it < polls; ++it) {
     uint32_t ok;
     asm volatile(
         "{ .reg .pred p; mbarrier.try_wait.parity.shared::cta.b64 p, [%1], 0; selp.b32 %0, 1, 0, p; }"
@@ -65,7 +69,24 @@ __device__ __forceinline__ bool mbar_wait0(uint64_t* bar, unsigned* err) {
     if (ok) return true;
     if (it > 64) __nanosleep(64);
   }
+  return false;
+}
+
+// The device control block of a mesh: err[0] error flags, err[1] the wait limit (0: the default,
+// k + 1: k polls).  Returns the number of polls of a kernel's staging waits.
+__device__ __forceinline__ uint32_t wait_polls(const unsigned* err) {
+  if (err == nullptr) return kDefaultWaitPolls;
+  const uint32_t lim = *(const volatile unsigned*)(err + 1);
+  return lim == 0u ? kDefaultWaitPolls : lim - 1u;
+}
+
+// Bounded wait for the bulk copies of a staging barrier.  If `polls` run out, sets bit 0 of *err
+// and waits once more (default limit) for the copies still in flight, so that no copy writes into
+// the shared memory of a CTA that has given up; returns false.
+__device__ __forceinline__ bool mbar_wait0(uint64_t* bar, unsigned* err, uint32_t polls) {
+  if (mbar_try0(bar, polls)) return true;
   if (err) atomicOr(err, 1u);
+  mbar_try0(bar, kDefaultWaitPolls);
   return false;
 }
 

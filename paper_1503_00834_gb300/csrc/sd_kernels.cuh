@@ -391,9 +391,11 @@ __global__ void __launch_bounds__(EPB * N * N) k_trace(const MeshArg<R> m, const
 // ------------------------------------------------------------------ staging
 
 // `between` runs after the copies are issued and before the wait (it issues the first sweep's
-// global loads so that both latencies overlap).
+// global loads so that both latencies overlap).  Returns false, the same in every thread of the CTA,
+// when the bounded wait for the copies ran out (the flag is set in *A.err and the copies in flight
+// have been waited for): the caller then skips its computation and every global store.
 template <int N, bool PERT, class R, int EPB, bool RES, class Between>
-__device__ __forceinline__ void stage_elements(const KArgs<R>& A, R* sm, uint64_t* bar, int ne, Between&& between) {
+__device__ __forceinline__ bool stage_elements(const KArgs<R>& A, R* sm, uint64_t* bar, int ne, Between&& between) {
   using L = Layout<N, PERT, R, EPB, RES>;
   constexpr int N3 = N * N * N;
   const int e0 = blockIdx.x * EPB;
@@ -430,8 +432,11 @@ __device__ __forceinline__ void stage_elements(const KArgs<R>& A, R* sm, uint64_
     for (int i = threadIdx.x; i < ne * 3 * N3; i += blockDim.x)
       sm[L::oGR0 + (i / (3 * N3)) * L::SGR0 + i % (3 * N3)] = (R)A.bg.grho0[(size_t)e0 * 3 * N3 + i];
   }
+  const uint32_t polls = wait_polls(A.err);
   between();
-  if (tq || tb || tg) mbar_wait0(bar, A.err);
+  bool ok = true;
+  if (tq || tb || tg) ok = mbar_wait0(bar, A.err, polls);
+  return __syncthreads_and(ok) != 0;
 }
 
 // ------------------------------------------------------------------ lifting, one direction
@@ -722,10 +727,10 @@ __global__ void __launch_bounds__(EPB * N * N, sizeof(R) == 4 ? grad_min_blocks<
   fill_tables<N, R>(A.ops, sm + Layout<N, PERT, R, EPB>::oTAB);
   __syncthreads();
   LiftPre<N, R> pre;
-  stage_elements<N, PERT, R, EPB, false>(A, sm, &bar, ne, [&] {
-    if (active) lift_prefetch<N, PERT, R, kLiftFused ? 1 : 0>(A, e, ln, pre);
-  });
-  __syncthreads();
+  if (!stage_elements<N, PERT, R, EPB, false>(A, sm, &bar, ne, [&] {
+        if (active) lift_prefetch<N, PERT, R, kLiftFused ? 1 : 0>(A, e, ln, pre);
+      }))
+    return;
   lift_all<N, PERT, R, EPB>(A, sm, el, ln, e, active, pre);
   // face metrics of the viscous-flux pass, loaded before the record stores
   R s3f[3][2][3];
@@ -985,14 +990,14 @@ __global__ void __launch_bounds__(EPB * N * N, sizeof(R) == 4 ? resid_min_blocks
   __syncthreads();
   FluxPre<R, (N == 4 && kEndFirstD0) || s3_ahead<N>() == 2> fp;
   __shared__ int snb[flux_nb_mode<N>() == 3 ? EPB : 1][12];  // (neighbour, face code) of the 6 faces
-  stage_elements<N, PERT, R, EPB, true>(A, sm, &bar, ne, [&] {
-    if (active) flux_prefetch<N, PERT, R, 0>(A, e, ln, fp);
-    if (flux_nb_mode<N>() == 3 && active && ln < 6) {
-      snb[el][2 * ln] = __ldg(A.m.nbr + e * 6 + ln);
-      snb[el][2 * ln + 1] = __ldg(A.m.code + e * 6 + ln);
-    }
-  });
-  __syncthreads();
+  if (!stage_elements<N, PERT, R, EPB, true>(A, sm, &bar, ne, [&] {
+        if (active) flux_prefetch<N, PERT, R, 0>(A, e, ln, fp);
+        if (flux_nb_mode<N>() == 3 && active && ln < 6) {
+          snb[el][2 * ln] = __ldg(A.m.nbr + e * 6 + ln);
+          snb[el][2 * ln + 1] = __ldg(A.m.code + e * 6 + ln);
+        }
+      }))
+    return;
   const int* snb_el = snb[flux_nb_mode<N>() == 3 ? el : 0];
   if (active) {
     flux_dir<N, PERT, R, EPB, 0, KR>(A, sm, el, ln, e, fp, snb_el);

@@ -8,7 +8,6 @@ missing the calls raise.
 from __future__ import annotations
 
 import ctypes
-import math
 import os
 
 import numpy as np
@@ -31,7 +30,8 @@ EXPORTS = ("chorus_mesh_create", "chorus_mesh_destroy", "chorus_mesh_info", "cho
            "chorus_closure_make_pairs", "chorus_closure_train", "chorus_closure_apply", "chorus_closure_attach", "chorus_batch_create",
            "chorus_batch_destroy", "chorus_batch_layout", "chorus_batch_init", "chorus_batch_rk_step",
            "chorus_batch_reduce", "chorus_batch_autotune", "chorus_set_well_balanced", "chorus_prepare_profile",
-           "chorus_afb_profile", "chorus_closure_set_scales")
+           "chorus_afb_profile", "chorus_closure_set_scales", "chorus_stable_dt_rule", "chorus_stable_dt",
+           "chorus_set_wait_limit", "chorus_fma_rate", "chorus_rk_step_host")
 
 
 class ChorusError(RuntimeError):
@@ -118,6 +118,11 @@ def load() -> ctypes.CDLL:
         "chorus_batch_rk_step": (i32, [vp, vp, vp, f64, i64, vp, P(i64)]),
         "chorus_batch_reduce": (i32, [vp, vp, P(f64), vp]),
         "chorus_batch_autotune": (i32, [vp, vp, vp, f64, i32, vp, P(i32)]),
+        "chorus_stable_dt_rule": (i32, [i32, f64, f64, f64, P(Params), P(f64)]),
+        "chorus_stable_dt": (i32, [vp, P(Params), P(f64)]),
+        "chorus_set_wait_limit": (i32, [vp, i64]),
+        "chorus_fma_rate": (i32, [i32, vp, P(f64)]),
+        "chorus_rk_step_host": (i32, [vp, P(Params), i32, vp, vp, vp, f64, i64, vp]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(lib, name)
@@ -212,6 +217,16 @@ class Mesh:
         _ok("chorus_rk_step", load().chorus_rk_step(self.handle, ctypes.byref(params), prec, _ptr(Q), _ptr(ws), dt,
                                                     n_steps, _stream(stream)))
 
+    def rk_step_host(self, params: Params, prec: int, Q_host, Q_dev, ws, dt: float, n_steps: int,
+                     stream=None) -> None:
+        """n_steps SSP-RK3 steps of a host-resident state (Q_host: contiguous CPU tensor, pinned for full
+        bandwidth): copied in, stepped on the device in Q_dev, copied back; synchronises."""
+        if Q_host.is_cuda or not Q_host.is_contiguous():
+            raise ValueError("Q_host must be a contiguous host tensor")
+        _ok("chorus_rk_step_host", load().chorus_rk_step_host(self.handle, ctypes.byref(params), prec,
+                                                              ctypes.c_void_p(Q_host.data_ptr()), _ptr(Q_dev),
+                                                              _ptr(ws), dt, n_steps, _stream(stream)))
+
     def rk_step_scheme(self, params: Params, prec: int, scheme: int, Q, ws, dt: float, n_steps: int,
                        stream=None) -> None:
         """scheme 0: SSP-RK3, 1: SSP-RK(5,4)."""
@@ -247,6 +262,17 @@ class Mesh:
 
     def check(self, stream=None) -> None:
         _ok("chorus_check", load().chorus_check(self.handle, _stream(stream)))
+
+    def stable_dt(self, params: Params) -> float:
+        """The library's fixed explicit time step for this mesh (chorus_stable_dt)."""
+        dt = ctypes.c_double()
+        _ok("chorus_stable_dt", load().chorus_stable_dt(self.handle, ctypes.byref(params), ctypes.byref(dt)))
+        return dt.value
+
+    def set_wait_limit(self, polls: int) -> None:
+        """Polls of the residual kernels' bounded staging waits (negative: the default; 0: give up at
+        once)."""
+        _ok("chorus_set_wait_limit", load().chorus_set_wait_limit(self.handle, polls))
 
 
 # ---------------------------------------------------------------- batched independent shells
@@ -409,27 +435,17 @@ def afb_profile(params: Params, r_inner: float, r_outer: float, n: int = 16385, 
     return r0, r1, rho, p
 
 
-def stable_dt(p: int, h_min: float, wave_speed: float, diffusivity: float) -> float:
-    """Fixed explicit step: 0.25 h/((2p+1) max(|u|+c)), capped by 0.25 h^2/((2p+1)^2 max(nu, kappa)).
-
-    h/((2p+1) c) is the one-dimensional limit; an element with comparable edges shares it among
-    three directions, so the factor is 0.25 (below 1/3).  A factor 0.5 diverged within 18-30 steps
-    at p = 4 and 5 on near-isotropic elements."""
-    dt = 0.25 * h_min / ((2 * p + 1) * wave_speed)
-    if diffusivity > 0:
-        dt = min(dt, 0.25 * h_min * h_min / ((2 * p + 1) ** 2 * diffusivity))
-    return dt
+def fma_rate(prec: int, stream=None) -> float:
+    """Measured FMA throughput of the current GPU in flop/s (chorus_fma_rate; FP64 or FP32)."""
+    r = ctypes.c_double()
+    _ok("chorus_fma_rate", load().chorus_fma_rate(prec, _stream(stream), ctypes.byref(r)))
+    return r.value
 
 
-def max_sound_speed(phys, r_inner: float, r_outer: float) -> float:
-    """Largest sound speed of the polytrope at rest (at the inner wall, where T is highest)."""
-    beta = r_inner / r_outer
-    d = r_outer - r_inner
-    n = phys.poly_n
-    chi_o = (beta + 1.0) / (beta * math.exp(phys.N_rho / n) + 1.0)
-    c = (2.0 * chi_o - beta - 1.0) / (1.0 - beta)
-    alpha = (1.0 + beta) * (1.0 - chi_o) / (1.0 - beta) ** 2
-    p_c = phys.GM * phys.rho_c / ((n + 1.0) * alpha * d)
-    T_c = p_c / (phys.R_gas * phys.rho_c)
-    chi_i = c + alpha * d / r_inner
-    return math.sqrt(phys.gamma * phys.R_gas * T_c * chi_i)
+def stable_dt(p: int, h_min: float, r_inner: float, r_outer: float, params: Params) -> float:
+    """The library's fixed explicit time step for order p and shortest element edge h_min
+    (chorus_stable_dt_rule, a host computation)."""
+    dt = ctypes.c_double()
+    _ok("chorus_stable_dt_rule", load().chorus_stable_dt_rule(p, h_min, r_inner, r_outer, ctypes.byref(params),
+                                                              ctypes.byref(dt)))
+    return dt.value

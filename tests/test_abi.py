@@ -64,3 +64,44 @@ def test_null_arguments(lib):
     assert lib.chorus_mesh_destroy(None) == 1
     assert lib.chorus_check(None, None) == 1
     assert lib.chorus_rk_workspace_bytes(None, 0) == 0
+
+
+def _params(phys):
+    from paper_1503_00834_gb300 import native
+
+    return native.Params.from_phys(phys)
+
+
+@pytest.mark.parametrize("p,nu", [(2, 5e-4), (3, 5e-4), (5, 5e-4), (3, 0.5)])
+def test_stable_dt_rule_matches_oracle(lib, p, nu):
+    """The time-step rule behind the C ABI against the oracle's, evaluated on the polytrope at rest at
+    the inner wall (where its sound speed peaks); nu = 0.5 takes the diffusive cap."""
+    import dataclasses
+
+    from chorus_inputs import make_phys
+    from oracle import state
+    from oracle.physics import Physics
+
+    phys = dataclasses.replace(make_phys(0.75, 1.5, 3.0, 1e-3), nu=nu)
+    ph = Physics.from_params(phys, 0.75, 1.0)
+    Q = state.background(ph, np.array([0.75, 0.0, 0.0]).reshape(1, 3, 1, 1, 1))
+    h = 0.0371
+    want = state.time_step(ph, p, h, Q)
+    got = ctypes.c_double()
+    assert lib.chorus_stable_dt_rule(p, h, 0.75, 1.0, ctypes.byref(_params(phys)), ctypes.byref(got)) == 0
+    assert abs(got.value - want) <= 1e-14 * want
+    if nu == 0.5:
+        assert abs(want - 0.25 * h * h / ((2 * p + 1) ** 2 * nu)) <= 1e-15 * want  # the cap is the branch taken
+
+
+def test_stable_dt_rule_rejects_bad_input(lib):
+    from chorus_inputs import make_phys
+
+    P = _params(make_phys(0.75, 1.5, 3.0, 1e-3))
+    dt = ctypes.c_double()
+    assert lib.chorus_stable_dt_rule(1, 0.1, 0.75, 1.0, ctypes.byref(P), ctypes.byref(dt)) == 1  # order
+    assert lib.chorus_stable_dt_rule(3, 0.0, 0.75, 1.0, ctypes.byref(P), ctypes.byref(dt)) == 1  # h_min
+    assert lib.chorus_stable_dt_rule(3, 0.1, 1.0, 0.75, ctypes.byref(P), ctypes.byref(dt)) == 1  # radii
+    assert lib.chorus_stable_dt_rule(3, 0.1, 0.75, 1.0, None, ctypes.byref(dt)) == 1
+    assert lib.chorus_stable_dt(None, ctypes.byref(P), ctypes.byref(dt)) == 1
+    assert lib.chorus_set_wait_limit(None, 5) == 1

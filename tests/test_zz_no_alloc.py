@@ -7,7 +7,9 @@ array.  This test calls the
 entry point through the C ABI twice in a row, on two different states, and checks each result
 against chorus_residual with a caller-provided workspace, within the parity tolerances the other
 GPU tests use (1e-12 relative for FP64, 1e-5 for the FP32 perturbation path).  It also checks that a
-mesh too large for the scratch is refused before any launch.  The file name makes pytest collect it
+mesh too large for the scratch is refused before any launch, that an attached learned closure is
+added exactly as chorus_residual adds it, and that a radial radiative diffusivity whose flux-point
+table has not been built is refused instead of allocated.  The file name makes pytest collect it
 last.
 """
 import ctypes
@@ -79,3 +81,63 @@ def test_noalloc_refuses_meshes_beyond_the_scratch():
     assert _noalloc(lib, sh, FP32_PERT, q, r) == 0
     sh.mesh.check()
     assert torch.isfinite(r).all()
+
+
+def test_noalloc_adds_an_attached_closure():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from chorus_inputs import small_shell
+    from paper_1503_00834_gb300 import FP32_PERT, FP64, Shell, build, load, native
+
+    build.build()
+    lib = load()
+    cfg = small_shell(2, 2, 2)  # p = 2, the closure's order
+    sh = Shell(cfg)
+    sh.mesh.prepare(sh.params)
+    w = native.closure_alloc(11, [1e-3] * 5, [2e-2] * 5)
+    native.closure_attach(sh.mesh, w)
+    try:
+        for prec, dtype, tol in ((FP64, torch.float64, 1e-12), (FP32_PERT, torch.float32, 1e-5)):
+            Q = torch.empty(sh.mesh.state_shape(), dtype=dtype, device="cuda")
+            sh.mesh.state_init(sh.params, cfg.seed, 1e-2, prec, Q)
+            ws = torch.empty(sh.mesh.workspace_bytes(prec), dtype=torch.uint8, device="cuda")
+            R_ref = torch.empty_like(Q)
+            sh.mesh.residual(sh.params, prec, Q, R_ref, ws)
+            native.closure_attach(sh.mesh, None)
+            R_plain = torch.empty_like(Q)
+            sh.mesh.residual(sh.params, prec, Q, R_plain, ws)
+            native.closure_attach(sh.mesh, w)
+            assert _rel(R_plain, R_ref) > 10 * tol  # the closure changes the residual: the check is not vacuous
+            for _ in range(2):
+                R = torch.full_like(Q, float("nan"))
+                assert _noalloc(lib, sh, prec, Q, R) == 0
+                sh.mesh.check()
+                assert _rel(R, R_ref) <= tol
+    finally:
+        native.closure_attach(sh.mesh, None)
+
+
+def test_noalloc_radial_kappa_r_needs_its_table():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from chorus_inputs import SHELL_288_P3 as cfg
+    from paper_1503_00834_gb300 import FP64, Shell, build, load
+
+    build.build()
+    lib = load()
+    sh = Shell(cfg)
+    sh.params.kappa_r1 = 2e-4  # kappa_r(r) = 2e-4 r: the flux-point table is needed
+    Q = torch.empty(sh.mesh.state_shape(), dtype=torch.float64, device="cuda")
+    R = torch.zeros_like(Q)
+    # no table yet: refused before any launch, nothing allocated
+    assert _noalloc(lib, sh, FP64, Q.fill_(1.0), R) == 1
+    assert not torch.any(R)
+    sh.mesh.state_init(sh.params, cfg.seed, cfg.entropy_amp, FP64, Q)  # prepares, building the table
+    ws = torch.empty(sh.mesh.workspace_bytes(FP64), dtype=torch.uint8, device="cuda")
+    R_ref = torch.empty_like(Q)
+    sh.mesh.residual(sh.params, FP64, Q, R_ref, ws)
+    for _ in range(2):
+        R = torch.full_like(Q, float("nan"))
+        assert _noalloc(lib, sh, FP64, Q, R) == 0
+        sh.mesh.check()
+        assert _rel(R, R_ref) <= 1e-12
