@@ -86,7 +86,10 @@ typedef struct {
  * (reference axes xi, eta, zeta).  Faces are paired by their corner nodes; unpaired faces must lie
  * on the sphere r_inner (inner wall) or r_outer (outer wall) to a relative 1e-6, else
  * CHORUS_EMESH.  metric_mode 0: conservative curl-form metrics (freestream preserving for every
- * p); 1: analytic cofactors of the 20-node map (freestream preserving for p >= 3).  The library
+ * p; for p >= 3 the curl form equals the cofactor rows exactly and is evaluated in that form, with
+ * less rounding); 1: analytic cofactors of the 20-node map (freestream preserving for p >= 3).
+ * The Jacobian and the metrics are formed from node coordinates measured from each element's node
+ * centroid (a translation, which leaves them unchanged but avoids cancellation in FP64).  The library
  * copies what it needs; the caller keeps ownership of its arrays.  Synchronises the stream. */
 chorus_status chorus_mesh_create(int64_t n_nodes, const double* node_xyz, int64_t n_elem,
                                  const int64_t* hex20, int p, double r_inner, double r_outer,

@@ -15,6 +15,15 @@ curl is taken exactly.  This makes the discrete metric identities hold, so a
 uniform flow is preserved on curved elements for every N, and the metric on a
 face depends only on that face's geometry.  The check variant
 `analytic_cofactors` evaluates x_eta x x_zeta etc. directly.
+
+Rounding: the Jacobian matrix and the curl-form products are formed from the node coordinates
+measured from the element's node centroid.  Eqs. 10-12 are invariant under a translation of x
+(d x / d xi is unchanged; curl I^N(c grad X_m) = 0 for the polynomial map), so the discrete metrics
+are the same, but the products X_l grad X_m are then of size h^2 instead of h, which removes the
+cancellation that otherwise costs a factor ~1/h of FP64 accuracy in the metrics.
+
+All geometry follows the dtype of the node coordinates (float64; np.longdouble for extended-
+precision runs of the oracle).
 """
 from __future__ import annotations
 
@@ -45,13 +54,14 @@ def shape_functions(xi, eta, zeta):
       corner:      (1/8)(1+a a_i)(1+b b_i)(1+c c_i)(a a_i + b b_i + c c_i - 2)
       mid-edge with a_i = 0: (1/4)(1-a^2)(1+b b_i)(1+c c_i), and likewise.
     """
-    a = 2.0 * np.asarray(xi, dtype=np.float64) - 1.0
-    b = 2.0 * np.asarray(eta, dtype=np.float64) - 1.0
-    c = 2.0 * np.asarray(zeta, dtype=np.float64) - 1.0
+    dt = np.result_type(np.asarray(xi), np.asarray(eta), np.asarray(zeta), np.float64)
+    a = 2.0 * np.asarray(xi, dtype=dt) - 1.0
+    b = 2.0 * np.asarray(eta, dtype=dt) - 1.0
+    c = 2.0 * np.asarray(zeta, dtype=dt) - 1.0
     a, b, c = np.broadcast_arrays(a, b, c)
     shp = a.shape + (20,)
-    Nv = np.zeros(shp)
-    dN = np.zeros(shp + (3,))
+    Nv = np.zeros(shp, dtype=dt)
+    dN = np.zeros(shp + (3,), dtype=dt)
     for i in range(20):
         ai, bi, ci = _NAT[i]
         if ai != 0 and bi != 0 and ci != 0:
@@ -104,13 +114,25 @@ def _grid(ops):
     return X[None, None, :], X[None, :, None], X[:, None, None]
 
 
+def centred(nodes: np.ndarray) -> np.ndarray:
+    """Node coordinates measured from each element's node centroid (a translation: same metrics)."""
+    return nodes - nodes.mean(axis=1, keepdims=True)
+
+
+def det3(J: np.ndarray) -> np.ndarray:
+    """Determinant of [..., 3, 3] matrices by cofactor expansion along the first row."""
+    return (J[..., 0, 0] * (J[..., 1, 1] * J[..., 2, 2] - J[..., 1, 2] * J[..., 2, 1])
+            - J[..., 0, 1] * (J[..., 1, 0] * J[..., 2, 2] - J[..., 1, 2] * J[..., 2, 0])
+            + J[..., 0, 2] * (J[..., 1, 0] * J[..., 2, 1] - J[..., 1, 1] * J[..., 2, 0]))
+
+
 def solution_geometry(nodes: np.ndarray, N: int):
     """x [E,3,N,N,N] and |J| [E,N,N,N] at the solution points (axes k, j, i)."""
-    ops = operators(N)
+    ops = operators(N, nodes.dtype.type)
     xi, eta, zeta = _grid(ops)
     x = map_points(nodes, xi, eta, zeta)  # [E,k,j,i,3]
-    Jm = jacobian_matrix(nodes, xi, eta, zeta)  # [E,k,j,i,3,3]
-    detJ = np.linalg.det(Jm)
+    Jm = jacobian_matrix(centred(nodes), xi, eta, zeta)  # [E,k,j,i,3,3]
+    detJ = det3(Jm)
     return np.moveaxis(x, -1, 1), detJ
 
 
@@ -123,10 +145,11 @@ def curl_metrics(nodes: np.ndarray, N: int):
       S_zeta [E,3(n),N+1(f),N(j),N(i)]   S^zeta_n at the zeta-flux points
       S_sol  [E,3(d),3(n),N,N,N]         S^d_n    at the solution points
     """
-    ops = operators(N)
+    ops = operators(N, nodes.dtype.type)
     Xf = ops.Xf
-    # geometry on the (N+1)^3 flux-point grid, axes (c, b, a) = (zeta, eta, xi)
-    X = map_points(nodes, Xf[None, None, :], Xf[:, None][None], Xf[:, None, None])  # [E,c,b,a,3]
+    dt = nodes.dtype
+    # geometry on the (N+1)^3 flux-point grid, axes (c, b, a) = (zeta, eta, xi), from the centroid
+    X = map_points(centred(nodes), Xf[None, None, :], Xf[:, None][None], Xf[:, None, None])  # [E,c,b,a,3]
     Dff = ops.Dff
     # derivatives of the grid interpolant of each coordinate: dX[e,c,b,a,m,dir]
     dX = np.stack(
@@ -139,10 +162,10 @@ def curl_metrics(nodes: np.ndarray, N: int):
     )
     E = nodes.shape[0]
     Lfs, Dfs = ops.Lfs, ops.Dfs
-    S_xi = np.zeros((E, 3, N, N, N + 1))
-    S_eta = np.zeros((E, 3, N, N + 1, N))
-    S_zeta = np.zeros((E, 3, N + 1, N, N))
-    S_sol = np.zeros((E, 3, 3, N, N, N))
+    S_xi = np.zeros((E, 3, N, N, N + 1), dtype=dt)
+    S_eta = np.zeros((E, 3, N, N + 1, N), dtype=dt)
+    S_zeta = np.zeros((E, 3, N + 1, N, N), dtype=dt)
+    S_sol = np.zeros((E, 3, 3, N, N, N), dtype=dt)
     for n in range(3):
         m, l = (n + 1) % 3, (n + 2) % 3
         V = X[..., l, None] * dX[..., m, :]  # [E,c,b,a,dir] = X_l * d X_m / d xi_dir

@@ -102,7 +102,7 @@ def primitives(Q: np.ndarray, ph: Physics):
 
 
 def conserved(rho, u, p, ph: Physics) -> np.ndarray:
-    Q = np.empty(np.shape(rho) + (5,))
+    Q = np.empty(np.shape(rho) + (5,), dtype=np.result_type(rho, u, p, np.float64))
     Q[..., 0] = rho
     Q[..., 1:4] = rho[..., None] * u
     Q[..., 4] = p / (ph.gamma - 1.0) + 0.5 * rho * np.sum(u * u, axis=-1)
@@ -112,7 +112,7 @@ def conserved(rho, u, p, ph: Physics) -> np.ndarray:
 def inviscid_flux(Q: np.ndarray, ph: Physics) -> np.ndarray:
     """Eq. 6: F_inv, G_inv, H_inv -> [..., 3(direction n), 5]."""
     rho, u, p = primitives(Q, ph)
-    F = np.empty(Q.shape[:-1] + (3, 5))
+    F = np.empty(Q.shape[:-1] + (3, 5), dtype=Q.dtype)
     for n in range(3):
         F[..., n, 0] = rho * u[..., n]
         for a in range(3):
@@ -168,7 +168,7 @@ def viscous_flux(Q: np.ndarray, gradW: np.ndarray, ph: Physics, kr=None) -> np.n
     rho, u, p = primitives(Q, ph)
     tau = stress(Q, gradW, ph)
     f = heat_flux(rho, p, gradW[..., 0, :], gradW[..., 4, :], ph, kr)
-    Fv = np.zeros(Q.shape[:-1] + (3, 5))
+    Fv = np.zeros(Q.shape[:-1] + (3, 5), dtype=np.result_type(Q, gradW))
     for n in range(3):
         for a in range(3):
             Fv[..., n, 1 + a] = tau[..., a, n]

@@ -44,12 +44,17 @@ from .sd_points import operators
 
 
 class Discretization:
-    """Mesh, operators and per-element geometry of one shell at order p."""
+    """Mesh, operators and per-element geometry of one shell at order p.
 
-    def __init__(self, node_xyz: np.ndarray, hex20: np.ndarray, p: int, r_inner: float, r_outer: float):
+    dtype: working precision of the operators and the geometry (float64; np.longdouble evaluates the
+    whole discretisation in extended precision from the same float64 node coordinates)."""
+
+    def __init__(self, node_xyz: np.ndarray, hex20: np.ndarray, p: int, r_inner: float, r_outer: float,
+                 dtype=np.float64):
         self.p = p
         self.N = p + 1
-        self.ops = operators(self.N)
+        self.dtype = dtype
+        self.ops = operators(self.N, dtype)
         self.node_xyz = np.asarray(node_xyz, dtype=np.float64)
         self.hex20 = np.asarray(hex20, dtype=np.int64)
         self.n_elem = self.hex20.shape[0]
@@ -61,7 +66,7 @@ class Discretization:
         """x, |J|, metrics at flux points and grad xi at solution points for `elems`."""
         key = elems.tobytes()
         if key not in self._geom:
-            nodes = self.node_xyz[self.hex20[elems]]
+            nodes = self.node_xyz[self.hex20[elems]].astype(self.dtype)
             x, detJ = solution_geometry(nodes, self.N)
             S_xi, S_eta, S_zeta, S_sol = curl_metrics(nodes, self.N)
             self._geom = {key: dict(x=x, detJ=detJ, S=(S_xi, S_eta, S_zeta),

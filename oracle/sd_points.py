@@ -19,14 +19,17 @@ import functools
 import numpy as np
 
 
-def solution_points(N: int) -> np.ndarray:
-    s = np.arange(1, N + 1, dtype=np.float64)
-    return 0.5 * (1.0 - np.cos((2.0 * s - 1.0) / (2.0 * N) * np.pi))
+def solution_points(N: int, dtype=np.float64) -> np.ndarray:
+    s = np.arange(1, N + 1).astype(dtype)
+    pi = np.arccos(dtype(-1))  # pi to the working precision
+    return 0.5 * (1.0 - np.cos((2.0 * s - 1.0) / (2.0 * N) * pi))
 
 
 def shifted_legendre(n: int, x):
     """P_n on [0,1] from the recurrence of Eq. 14 (P_{-1} = 0, P_0 = 1)."""
-    x = np.asarray(x, dtype=np.float64)
+    x = np.asarray(x)
+    if x.dtype.kind != "f":
+        x = x.astype(np.float64)
     p_prev = np.zeros_like(x)
     p = np.ones_like(x)
     for m in range(1, n + 1):
@@ -34,12 +37,12 @@ def shifted_legendre(n: int, x):
     return p
 
 
-def flux_points(N: int) -> np.ndarray:
+def flux_points(N: int, dtype=np.float64) -> np.ndarray:
     """End points plus the roots of P_{N-1}; roots bracketed on a fine grid, then bisected."""
     n = N - 1
     roots = []
     if n >= 1:
-        grid = np.linspace(0.0, 1.0, 200 * N + 1)
+        grid = np.linspace(dtype(0), dtype(1), 200 * N + 1, dtype=dtype)
         vals = shifted_legendre(n, grid)
         for a, b, fa, fb in zip(grid[:-1], grid[1:], vals[:-1], vals[1:]):
             if fa == 0.0:
@@ -58,12 +61,12 @@ def flux_points(N: int) -> np.ndarray:
                         hi = mid
                 roots.append(0.5 * (lo + hi))
     assert len(roots) == n, (N, roots)
-    return np.array([0.0] + sorted(roots) + [1.0])
+    return np.array([dtype(0)] + sorted(roots) + [dtype(1)], dtype=dtype)
 
 
 def lagrange(nodes: np.ndarray, i: int, x):
     """Lagrange cardinal polynomial through `nodes`, index i, at x (Eqs. 15, 16)."""
-    x = np.asarray(x, dtype=np.float64)
+    x = np.asarray(x, dtype=nodes.dtype)
     out = np.ones_like(x)
     for s in range(len(nodes)):
         if s != i:
@@ -73,7 +76,7 @@ def lagrange(nodes: np.ndarray, i: int, x):
 
 def lagrange_deriv(nodes: np.ndarray, i: int, x):
     """d/dx of the Lagrange cardinal polynomial: product rule over the factors."""
-    x = np.asarray(x, dtype=np.float64)
+    x = np.asarray(x, dtype=nodes.dtype)
     total = np.zeros_like(x)
     for m in range(len(nodes)):
         if m == i:
@@ -95,12 +98,15 @@ class Operators:
     Dff[a, b] = l'_b(Xf_a)       derivative on the flux-point grid (N+1, N+1)
     Dfs[s, a] = l'_a(X_s)        derivative of flux-point polynomials at solution points (N, N+1)
     w[s]      = int_0^1 h_s dX   interpolatory quadrature weights at the solution points
+
+    dtype: the working precision of the points and matrices (float64; np.longdouble for extended-
+    precision runs of the oracle).  The weights are computed in float64 (they enter only integrals).
     """
 
-    def __init__(self, N: int):
+    def __init__(self, N: int, dtype=np.float64):
         self.N = N
-        self.Xs = solution_points(N)
-        self.Xf = flux_points(N)
+        self.Xs = solution_points(N, dtype)
+        self.Xf = flux_points(N, dtype)
         Xs, Xf = self.Xs, self.Xf
         self.I = np.array([[lagrange(Xs, s, Xf[f]) for s in range(N)] for f in range(N + 1)])
         self.D = np.array([[lagrange_deriv(Xf, f, Xs[s]) for f in range(N + 1)] for s in range(N)])
@@ -111,9 +117,10 @@ class Operators:
         gx, gw = np.polynomial.legendre.leggauss(N)
         gx = 0.5 * (gx + 1.0)
         gw = 0.5 * gw
-        self.w = np.array([np.sum(gw * lagrange(Xs, s, gx)) for s in range(N)])
+        Xs64 = Xs.astype(np.float64)
+        self.w = np.array([np.sum(gw * lagrange(Xs64, s, gx)) for s in range(N)])
 
 
 @functools.lru_cache(maxsize=None)
-def operators(N: int) -> Operators:
-    return Operators(N)
+def operators(N: int, dtype=np.float64) -> Operators:
+    return Operators(N, dtype)

@@ -253,16 +253,24 @@ int build_mesh(int64_t n_nodes, const double* node_xyz, int64_t n_elem, const in
   const auto& Lfs = tab.Lfs;
 #pragma omp parallel for schedule(static) reduction(| : bad)
   for (int64_t e = 0; e < E; ++e) {
-    double X[20][3];
+    // node coordinates, and the same measured from the element's node centroid: the Jacobian and
+    // the metrics are invariant under that translation (Eqs. 10-12), and with centred coordinates
+    // their sums do not cancel from O(|x|) down to O(h), which keeps them accurate to a few ulp
+    double X[20][3], Xc[20][3], cen[3] = {0, 0, 0};
     for (int a = 0; a < 20; ++a)
-      for (int c = 0; c < 3; ++c) X[a][c] = node_xyz[3 * hex20[e * 20 + a] + c];
+      for (int c = 0; c < 3; ++c) {
+        X[a][c] = node_xyz[3 * hex20[e * 20 + a] + c];
+        cen[c] += X[a][c];
+      }
+    for (int a = 0; a < 20; ++a)
+      for (int c = 0; c < 3; ++c) Xc[a][c] = X[a][c] - cen[c] / 20.0;
     // solution-point coordinates and |J|
     for (int pt = 0; pt < N3; ++pt) {
       double xx[3] = {0, 0, 0}, J[3][3] = {{0, 0, 0}, {0, 0, 0}, {0, 0, 0}};
       for (int a = 0; a < 20; ++a) {
         for (int c = 0; c < 3; ++c) {
           xx[c] += Nsol[pt * 20 + a] * X[a][c];
-          for (int d = 0; d < 3; ++d) J[c][d] += dNsol[(pt * 20 + a) * 3 + d] * X[a][c];
+          for (int d = 0; d < 3; ++d) J[c][d] += dNsol[(pt * 20 + a) * 3 + d] * Xc[a][c];
         }
       }
       const double det = J[0][0] * (J[1][1] * J[2][2] - J[1][2] * J[2][1]) -
@@ -274,7 +282,10 @@ int build_mesh(int64_t n_nodes, const double* node_xyz, int64_t n_elem, const in
     }
     double* Se = &M.Sf[(size_t)e * 9 * NF * N2];
     auto Sat = [&](int d, int n, int f, int ln) -> double& { return Se[((d * 3 + n) * NF + f) * N2 + ln]; };
-    if (metric_mode == 1) {
+    // For N >= 4 the curl form's interpolation of X_l grad X_m is exact (the 20-node map has degree
+    // <= 2 in each reference variable, so the products have degree <= 4), and its exact curl equals
+    // the cofactor rows grad X_m x grad X_l: the same metrics, evaluated with far less rounding.
+    if (metric_mode == 1 || N >= 4) {
       // analytic cofactor rows: S^0 = a_1 x a_2, S^1 = a_2 x a_0, S^2 = a_0 x a_1 with a_d = dx/dxi_d
       for (int d = 0; d < 3; ++d)
         for (int f = 0; f < NF; ++f)
@@ -282,7 +293,7 @@ int build_mesh(int64_t n_nodes, const double* node_xyz, int64_t n_elem, const in
             double J[3][3] = {{0, 0, 0}, {0, 0, 0}, {0, 0, 0}};
             for (int a = 0; a < 20; ++a)
               for (int c = 0; c < 3; ++c)
-                for (int dd = 0; dd < 3; ++dd) J[c][dd] += dNfl[(((d * NF + f) * N2 + ln) * 20 + a) * 3 + dd] * X[a][c];
+                for (int dd = 0; dd < 3; ++dd) J[c][dd] += dNfl[(((d * NF + f) * N2 + ln) * 20 + a) * 3 + dd] * Xc[a][c];
             const int u = (d + 1) % 3, w = (d + 2) % 3;
             for (int n = 0; n < 3; ++n) {
               const int n1 = (n + 1) % 3, n2 = (n + 2) % 3;
@@ -297,7 +308,7 @@ int build_mesh(int64_t n_nodes, const double* node_xyz, int64_t n_elem, const in
     for (int g = 0; g < G; ++g)
       for (int c = 0; c < 3; ++c) {
         double s = 0;
-        for (int a = 0; a < 20; ++a) s += Ngrid[g * 20 + a] * X[a][c];
+        for (int a = 0; a < 20; ++a) s += Ngrid[g * 20 + a] * Xc[a][c];
         Xg[g * 3 + c] = s;
       }
     auto gid = [&](int a, int b, int c) { return (c * NF + b) * NF + a; };

@@ -97,9 +97,25 @@ constexpr int kS3AheadN5 = 1;
 template <int N>
 __host__ __device__ constexpr int s3_ahead() { return N == 4 ? kS3AheadN4 : N == 5 ? kS3AheadN5 : 1; }
 
+// Whether the residual kernel stages each direction's metric block S^D_n (3 x (N+1) x N^2 words per
+// element, contiguous in global memory) in shared memory by bulk copies, double-buffered across the
+// three sweeps (direction 0 with the element blocks, 1 during sweep 0, 2 during sweep 1), instead of
+// loading the metrics of each flux point from global memory ahead of use.
+constexpr bool kStageMetricsN4 = true;
+template <int N, class R>
+__host__ __device__ constexpr bool stage_metrics() { return sizeof(R) == 4 && N == 4 && kStageMetricsN4; }
+
 // Lifting order: false = directions 0, 1, 2 and a separate pass that forms the gradient record;
 // true = directions 1, 2, 0 with the record formed in the last sweep.
 constexpr bool kLiftFused = true;
+
+// Lifting with raw partial derivatives (with the fused order only): the first two sweeps store, per
+// point, their five derivatives d q_v / d xi_D and the three components of grad xi_D (8 words, no
+// read-modify-write), and the last sweep forms the conserved gradients from them and its own:
+// 44 shared-memory accesses per point instead of 72 for the 15 accumulated components.
+constexpr bool kLiftRaw = true;
+template <int N, class R>
+__host__ __device__ constexpr bool lift_raw() { return kLiftRaw && kLiftFused && sizeof(R) == 4 && N == 4; }
 
 // Whether the lifting kernel writes the gradient record with bulk stores from shared memory (timed
 // per order: 1-4 % faster at N = 3, 4, 6, 3 % slower at N = 5).
@@ -115,8 +131,11 @@ struct Layout {
   static constexpr int SQ = pad_stride<R>(5 * N3);
   static constexpr int SBG = bgShared ? pad_stride<R>(2 * N3) : 0;
   static constexpr int SGR0 = bgShared ? pad_stride<R>(3 * N3) : 0;
-  static constexpr int SG = pad_stride<R>((RES ? kG : 15) * N3);
+  static constexpr int SG = pad_stride<R>((RES ? kG : (lift_raw<N, R>() ? 16 : 15)) * N3);
   static constexpr int SDIV = pad_stride<R>(5 * N3);
+  // staged metric blocks of one direction (residual kernel, when stage_metrics)
+  static constexpr bool SM = RES && stage_metrics<N, R>();
+  static constexpr int SSF = SM ? 3 * (N + 1) * N2 : 0;
   // interpolation I[f][s] and derivative D[i][f] tables, indexed at run time by rolled loops
   static constexpr int TAB = pad_stride<R>(2 * (N + 1) * N);
   static constexpr int oTAB = 0;
@@ -126,7 +145,9 @@ struct Layout {
   static constexpr int oG = oGR0 + EPB * SGR0;
   static constexpr int oDIV = oG + EPB * SG;
   static constexpr int total_grad = oDIV;
-  static constexpr int total_resid = oDIV + EPB * SDIV;
+  static constexpr int oSF0 = oDIV + EPB * SDIV;
+  static constexpr int oSF1 = oSF0 + EPB * SSF;
+  static constexpr int total_resid = oSF1 + EPB * SSF;
   // per-element bulk copies need 16-byte element blocks in global memory
   static constexpr bool tmaQ = (5 * N3 * sizeof(R)) % 16 == 0;
   static constexpr bool tmaBG = (2 * N3 * sizeof(R)) % 16 == 0 && (3 * N3 * sizeof(R)) % 16 == 0;
@@ -334,9 +355,11 @@ __device__ __forceinline__ void flux_prefetch(const KArgs<R>& A, int e, int ln, 
   constexpr int N2 = N * N;
   constexpr bool EF = end_first<N, D>();
   const R* Sl = A.m.Sf + ((size_t)e * 3 + D) * 3 * (N + 1) * N2;
+  if constexpr (!stage_metrics<N, R>()) {
 #pragma unroll
-  for (int n = 0; n < 3; ++n) p.s3[n] = __ldg(Sl + (n * (N + 1) + flux_order<N, EF>(0)) * N2 + ln);
-  if constexpr (s3_ahead<N>() == 2) {
+    for (int n = 0; n < 3; ++n) p.s3[n] = __ldg(Sl + (n * (N + 1) + flux_order<N, EF>(0)) * N2 + ln);
+  }
+  if constexpr (!stage_metrics<N, R>() && s3_ahead<N>() == 2) {
 #pragma unroll
     for (int n = 0; n < 3; ++n) p.s3b[n] = __ldg(Sl + (n * (N + 1) + flux_order<N, EF>(1)) * N2 + ln);
   }
@@ -406,12 +429,18 @@ __device__ __forceinline__ bool stage_elements(const KArgs<R>& A, R* sm, uint64_
     for (int i = threadIdx.x; i < ne * kG * N3; i += blockDim.x)
       sm[L::oG + (i / (kG * N3)) * L::SG + i % (kG * N3)] = A.G_in[(size_t)e0 * kG * N3 + i];
   }
-  if (threadIdx.x == 0 && (tq || tb || tg)) {
+  const bool any_bulk = tq || tb || tg || L::SM;
+  if (threadIdx.x == 0 && any_bulk) {
     uint32_t bytes = 0;
     if (tq) bytes += ne * 5 * N3 * sizeof(R);
     if (tb) bytes += ne * 5 * N3 * sizeof(R);
     if (tg) bytes += ne * kG * N3 * sizeof(R);
+    if (L::SM) bytes += ne * L::SSF * sizeof(R);
     mbar_expect_tx(bar, bytes);
+    if constexpr (L::SM) {
+      for (int el = 0; el < ne; ++el)
+        bulk_g2s(sm + L::oSF0 + el * L::SSF, A.m.Sf + ((size_t)(e0 + el) * 3) * L::SSF, L::SSF * sizeof(R), bar);
+    }
     for (int el = 0; el < ne; ++el) {
       if (tg) bulk_g2s(sm + L::oG + el * L::SG, A.G_in + (size_t)(e0 + el) * kG * N3, kG * N3 * sizeof(R), bar);
       if (tq) bulk_g2s(sm + L::oQ + el * L::SQ, A.q + (size_t)(e0 + el) * 5 * N3, 5 * N3 * sizeof(R), bar);
@@ -435,7 +464,7 @@ __device__ __forceinline__ bool stage_elements(const KArgs<R>& A, R* sm, uint64_
   const uint32_t polls = wait_polls(A.err);
   between();
   bool ok = true;
-  if (tq || tb || tg) ok = mbar_wait0(bar, A.err, polls);
+  if (any_bulk) ok = mbar_wait0(bar, A.err, polls);
   return __syncthreads_and(ok) != 0;
 }
 
@@ -527,18 +556,41 @@ __device__ __forceinline__ void lift_dir(const KArgs<R>& A, R* sm, int el, int l
     }
     const int si = line_sidx<N, D, R>(ln, i);
     R gq[LAST ? 15 : 1];
+    constexpr bool RAW = lift_raw<N, R>();
+    R dvv[5];
 #pragma unroll
     for (int v = 0; v < 5; ++v) {
       R dv = A.ops.D[i][0] * dq[v][0] + A.ops.D[i][N] * dq[v][1];
 #pragma unroll
       for (int s = 0; s < N; ++s) dv += A.ops.Dsol[i][s] * qv[v][s];
+      dvv[v] = dv;
+      if constexpr (!RAW) {
 #pragma unroll
-      for (int n = 0; n < 3; ++n) {
-        R* p = sg + (3 * v + n) * N3 + si;
-        if constexpr (LAST) gq[3 * v + n] = *p + dv * gx[n];
-        else if constexpr (FIRST) *p = dv * gx[n];
-        else *p += dv * gx[n];
+        for (int n = 0; n < 3; ++n) {
+          R* p = sg + (3 * v + n) * N3 + si;
+          if constexpr (LAST) gq[3 * v + n] = *p + dv * gx[n];
+          else if constexpr (FIRST) *p = dv * gx[n];
+          else *p += dv * gx[n];
+        }
       }
+    }
+    if constexpr (RAW && !LAST) {
+      // slot 0 (first sweep) or 1: the five derivatives, then grad xi_D
+      constexpr int o = FIRST ? 0 : 8;
+#pragma unroll
+      for (int v = 0; v < 5; ++v) sg[(o + v) * N3 + si] = dvv[v];
+#pragma unroll
+      for (int n = 0; n < 3; ++n) sg[(o + 5 + n) * N3 + si] = gx[n];
+    }
+    if constexpr (RAW && LAST) {
+      R raw[16];
+#pragma unroll
+      for (int c = 0; c < 16; ++c) raw[c] = sg[c * N3 + si];
+#pragma unroll
+      for (int v = 0; v < 5; ++v)
+#pragma unroll
+        for (int n = 0; n < 3; ++n)
+          gq[3 * v + n] = dvv[v] * gx[n] + raw[v] * raw[5 + n] + raw[8 + v] * raw[13 + n];
     }
     if constexpr (LAST) {
       if (A.grad_rho_out) {
@@ -774,8 +826,9 @@ __global__ void __launch_bounds__(EPB * N * N, sizeof(R) == 4 ? grad_min_blocks<
 // points (Eq. 18), accumulated into the divergence array.
 template <int N, bool PERT, class R, int EPB, int D, bool KR, bool X>
 __device__ __forceinline__ void flux_dir(const KArgs<R>& A, R* sm, int el, int ln, int e, const FluxPre<R, X>& pre,
-                                         const int* snb) {
+                                         const int* snb, const R* sS) {
   using L = Layout<N, PERT, R, EPB, true>;
+  constexpr bool SMM = L::SM;  // metrics of this direction staged in shared memory at sS
   constexpr int N2 = N * N, N3 = N * N * N;
   const R* sq = sm + L::oQ + el * L::SQ;
   const R* sbg = sm + L::oBG + el * L::SBG;
@@ -808,8 +861,12 @@ __device__ __forceinline__ void flux_dir(const KArgs<R>& A, R* sm, int el, int l
   // Flux points in the order 1, ..., N, 0, so that the neighbour data (prefetched) are first needed
   // after the interior points; S^D at the next flux point is loaded one iteration ahead.
   constexpr bool EF = end_first<N, D>();
-  constexpr int AH = s3_ahead<N>();
-  R s3n[3] = {pre.s3[0], pre.s3[1], pre.s3[2]};
+  constexpr int AH = SMM ? 0 : s3_ahead<N>();
+  R s3n[3];
+  if constexpr (!SMM) {
+#pragma unroll
+    for (int n = 0; n < 3; ++n) s3n[n] = pre.s3[n];
+  }
   R s3nn[AH == 2 ? 3 : 1];
   if constexpr (AH == 2) {
 #pragma unroll
@@ -820,8 +877,16 @@ __device__ __forceinline__ void flux_dir(const KArgs<R>& A, R* sm, int el, int l
 #pragma unroll 1
   for (int it = 0; it <= N; ++it) {
     const int f = flux_order<N, EF>(it);
-    R s3[3] = {s3n[0], s3n[1], s3n[2]};
-    if constexpr (AH == 2) {
+    R s3[3];
+    if constexpr (SMM) {
+#pragma unroll
+      for (int n = 0; n < 3; ++n) s3[n] = sS[(n * (N + 1) + f) * N2 + ln];
+    } else {
+#pragma unroll
+      for (int n = 0; n < 3; ++n) s3[n] = s3n[n];
+    }
+    if constexpr (SMM) {
+    } else if constexpr (AH == 2) {
 #pragma unroll
       for (int n = 0; n < 3; ++n) s3n[n] = s3nn[n];
       if (it + 2 <= N) {
@@ -979,16 +1044,38 @@ __global__ void __launch_bounds__(EPB * N * N, sizeof(R) == 4 ? resid_min_blocks
   constexpr int N2 = N * N, N3 = N * N * N;
   extern __shared__ __align__(128) unsigned char smem_raw[];
   __shared__ __align__(8) uint64_t bar;
+  __shared__ __align__(8) uint64_t barS[L::SM ? 2 : 1];  // staged metrics of directions 1 and 2
   R* sm = reinterpret_cast<R*>(smem_raw);
   const int el = threadIdx.x / N2, ln = threadIdx.x % N2;
   const int e0 = blockIdx.x * EPB;
   const int ne = min(EPB, A.m.E - e0);
   const int e = e0 + el;
   const bool active = el < ne;
-  if (threadIdx.x == 0) mbar_init(&bar);
+  if (threadIdx.x == 0) {
+    mbar_init(&bar);
+    if constexpr (L::SM) {
+      mbar_init(&barS[0]);
+      mbar_init(&barS[1]);
+    }
+  }
   fill_tables<N, R>(A.ops, sm + L::oTAB);
   __syncthreads();
-  FluxPre<R, (N == 4 && kEndFirstD0) || s3_ahead<N>() == 2> fp;
+  // direction d's metric blocks of the CTA's elements into buffer `buf` (thread 0), on barrier b
+  auto stage_dir = [&](int d, int buf, uint64_t* b) {
+    if constexpr (L::SM) {
+      if (threadIdx.x == 0) {
+        fence_async_smem();  // the buffer's previous contents were read by the generic proxy
+        mbar_expect_tx(b, ne * L::SSF * sizeof(R));
+        for (int j = 0; j < ne; ++j)
+          bulk_g2s(sm + (buf ? L::oSF1 : L::oSF0) + j * L::SSF, A.m.Sf + ((size_t)(e0 + j) * 3 + d) * L::SSF,
+                   L::SSF * sizeof(R), b);
+      }
+    }
+  };
+  const R* sS0 = sm + L::oSF0 + el * L::SSF;
+  const R* sS1 = sm + L::oSF1 + el * L::SSF;
+  bool failed = false;
+  FluxPre<R, !stage_metrics<N, R>() && ((N == 4 && kEndFirstD0) || s3_ahead<N>() == 2)> fp;
   __shared__ int snb[flux_nb_mode<N>() == 3 ? EPB : 1][12];  // (neighbour, face code) of the 6 faces
   if (!stage_elements<N, PERT, R, EPB, true>(A, sm, &bar, ne, [&] {
         if (active) flux_prefetch<N, PERT, R, 0>(A, e, ln, fp);
@@ -998,18 +1085,23 @@ __global__ void __launch_bounds__(EPB * N * N, sizeof(R) == 4 ? resid_min_blocks
         }
       }))
     return;
+  const uint32_t polls = wait_polls(A.err);
   const int* snb_el = snb[flux_nb_mode<N>() == 3 ? el : 0];
+  stage_dir(1, 1, &barS[0]);
   if (active) {
-    flux_dir<N, PERT, R, EPB, 0, KR>(A, sm, el, ln, e, fp, snb_el);
+    flux_dir<N, PERT, R, EPB, 0, KR>(A, sm, el, ln, e, fp, snb_el, sS0);
     flux_prefetch<N, PERT, R, 1>(A, e, ln, fp);
   }
   __syncthreads();
+  stage_dir(2, 0, &barS[1]);
+  if constexpr (L::SM) failed |= !mbar_wait0(&barS[0], A.err, polls);
   if (active) {
-    flux_dir<N, PERT, R, EPB, 1, KR>(A, sm, el, ln, e, fp, snb_el);
+    flux_dir<N, PERT, R, EPB, 1, KR>(A, sm, el, ln, e, fp, snb_el, sS1);
     flux_prefetch<N, PERT, R, 2>(A, e, ln, fp);
   }
   __syncthreads();
-  if (active) flux_dir<N, PERT, R, EPB, 2, KR>(A, sm, el, ln, e, fp, snb_el);
+  if constexpr (L::SM) failed |= !mbar_wait0(&barS[1], A.err, polls);
+  if (active) flux_dir<N, PERT, R, EPB, 2, KR>(A, sm, el, ln, e, fp, snb_el, sS0);
 
   // Global inputs of the epilogue, all issued before its first store.  The epilogue works point by
   // point, so thread ln takes the points ln + N^2 i (i < N): 16 consecutive threads read 64
@@ -1026,11 +1118,13 @@ __global__ void __launch_bounds__(EPB * N * N, sizeof(R) == 4 ? resid_min_blocks
       for (int v = 0; v < 5; ++v) {
         const size_t oi = ((size_t)e * 5 + v) * N3 + pt;
         r0g[v][i] = (PERT && A.bg.R0) ? (R)__ldg(A.bg.R0 + oi) : R(0);
-        ung[v][i] = (MODE == kModeRK) ? A.un[oi] : R(0);
+        // a stage whose combination has no u^n term (a = 0) does not read it
+        ung[v][i] = (MODE == kModeRK && A.a != R(0)) ? A.un[oi] : R(0);
       }
     }
   }
-  __syncthreads();
+  // a staged-metric wait that gave up (flag set, copies drained): no thread stores anything
+  if (__syncthreads_or(failed)) return;
 
   // residual dQ/dt = -div/|J| - M (Eqs. 4, 11), sources of Eqs. 2-3, and the RK combination
   R* sq = sm + L::oQ + el * L::SQ;

@@ -1,6 +1,5 @@
 """Pins of the oracle's residual and time stepping against what the paper fixes.
 
-  * freestream preservation on the curved shell (Eq. 12 with the curl-form metrics)
   * discrete conservation of mass, and of energy up to the gravity work (Eq. 4 in
     conservative form, single-valued common fluxes, walls with V_r = 0)
   * hydrostatic balance of the polytrope (Eqs. 20, 25-27) converging under
@@ -36,26 +35,6 @@ def _weights(disc):
     g = disc.geometry(np.arange(disc.n_elem))
     w = disc.ops.w
     return w[None, :, None, None] * w[None, None, :, None] * w[None, None, None, :] * g["detJ"], g
-
-
-@pytest.mark.parametrize("p", [2, 3])
-@pytest.mark.parametrize("viscous", [False, True])
-def test_freestream_preservation(p, viscous):
-    n_r = 5
-    disc = _disc(2, n_r, p)
-    ph = _phys(nu=1e-2 if viscous else 0.0, kappa=1e-2 if viscous else 0.0, GM=0.0, Omega=0.0)
-    N, E = disc.N, disc.n_elem
-    u = np.broadcast_to(np.array([0.3, -0.2, 0.1]), (E, N, N, N, 3))
-    Q = np.moveaxis(conserved(np.full((E, N, N, N), 1.3), u, np.full((E, N, N, N), 0.9), ph), -1, 1).copy()
-    R = residual(disc, ph, Q)
-    k = np.arange(E) % n_r
-    hops = 2 if viscous else 1  # walls break the uniform state; BR1 reaches two face hops
-    interior = (k >= hops) & (k < n_r - hops)
-    h_min = state.min_edge_chord(disc.node_xyz, disc.hex20)
-    scale = np.abs(inviscid_flux(np.moveaxis(Q[0, :, 0, 0, 0], 0, -1), ph)).max() * N * N / h_min
-    assert np.abs(R[interior]).max() < 1e-13 * scale
-    # and the walls do act on the wall layers (the check above is not vacuous)
-    assert np.abs(R[k == 0]).max() > 1e-3
 
 
 def test_mass_and_energy_conservation():
@@ -122,8 +101,9 @@ def test_manufactured_solution_convergence(p, viscous):
     e1, _ = _mms_error(4, 6, p, ph)
     e2, s2 = _mms_error(8, 12, p, ph)
     rates = np.log2(e1 / e2)
-    # inviscid residual truncation falls as h^p; the lifted (BR1) second derivatives lose up to one order
-    assert np.all(rates > (p - 1.3 if viscous else p - 0.5)), rates
+    # inviscid residual truncation falls as h^p; the lifted (BR1) second derivatives lose one order
+    # (isolated and measured at p - 1 in test_oracle_diffusion.py)
+    assert np.all(rates > (p - 1.2 if viscous else p - 0.5)), rates
     assert np.all(e2 < 0.05 * s2), (e2, s2)
 
 
