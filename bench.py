@@ -393,15 +393,15 @@ def stage_roofline(alg_bytes_per_dof: float, n_dof: int, stage_ms: float, peak: 
     its time, measured DRAM bytes (ncu, when taken on these sources) and their rate."""
     achieved = alg_bytes_per_dof * n_dof / (stage_ms / 1e3) / 1e9
     tr_stage = None
-    if traffic and all(traffic.get(k) is not None for k in ("k_grad", "k_resid")):
-        tr_stage = traffic["k_grad"] + traffic["k_resid"]
+    if traffic and all(traffic.get(k) is not None for k in ("k_grad", "k_face", "k_resid")):
+        tr_stage = traffic["k_grad"] + traffic["k_face"] + traffic["k_resid"]
     per = {}
     for name, ms in kernels.items():
         b = traffic.get(name) if traffic else None
         per[name] = {"launch_ms": ms, "dram_bytes": b,
                      "dram_gbs": (b / (ms / 1e3) / 1e9) if (b and ms) else None,
                      "dram_frac": (b / (ms / 1e3) / 1e9 / peak) if (b and ms) else None}
-    return {"bound": "hbm", "kernel": "whole RK stage (k_grad + k_resid per stage; k_trace once per call)",
+    return {"bound": "hbm", "kernel": "whole RK stage (k_grad + k_face + k_resid per stage; k_trace once per call)",
             "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak, "traffic": tr_stage,
             "peak_kind": peak_kind, "alg_bytes_per_dof_stage": alg_bytes_per_dof, "stage_ms": stage_ms,
             "kernels": per}
@@ -490,7 +490,7 @@ def main():
         torch.cuda.synchronize()
         kms, kcnt = mesh.timing_read()
         mesh.timing_enable(False)
-        per = {nm: kms[c] / max(1, kcnt[c]) for c, nm in enumerate(("k_trace", "k_grad", "k_resid"))}
+        per = {nm: kms[c] / max(1, kcnt[c]) for c, nm in enumerate(("k_trace", "k_grad", "k_resid", "k_face"))}
         return ev0.elapsed_time(ev1), per, sum(kcnt)
 
     # ---- warm-up, then K timed steps (inputs far larger than L2: state 425 MB FP32)
@@ -513,7 +513,7 @@ def main():
     alg = (ALG_BYTES_PER_DOF_STAGE if prec == FP32_PERT else ALG_BYTES_PER_DOF_STAGE_FP64)[cfg.p]
     peak, peak_kind = _peaks()
     tpath = os.path.join(ROOT, "profiles", "traffic.json")
-    traffic = {k: lookup_traffic(tpath, k, cfg.name, args.prec) for k in ("k_grad", "k_resid")}
+    traffic = {k: lookup_traffic(tpath, k, cfg.name, args.prec) for k in ("k_grad", "k_face", "k_resid")}
     roof = stage_roofline(alg, n_dof, ms / stages, peak, peak_kind, kper, traffic)
 
     # ---- FP64 GPU path on the same workload (the metric compares both), with its FP64-unit roofline

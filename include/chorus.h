@@ -275,9 +275,10 @@ chorus_status chorus_closure_attach(chorus_mesh coarse, const void* weights);
 /* Kernel timing for measurement.  While enabled, every kernel that chorus_residual and
  * chorus_rk_step launch is bracketed by a pair of CUDA events recorded on the call's stream (the
  * kernels themselves are unchanged).  chorus_timing_read synchronises the stream and returns, per
- * kernel class (0: face traces, 1: lifted gradients / one-sided viscous fluxes, 2: residual and RK
- * update), the summed device milliseconds and launch counts recorded since the last read, then
- * clears them.  ms, counts: host arrays of 3.  enable = 0 stops recording. */
+ * kernel class (0: face traces, 1: lifted gradients / one-sided viscous fluxes / wall fluxes,
+ * 2: residual and RK update, 3: common fluxes of the interior faces), the summed device
+ * milliseconds and launch counts recorded since the last read, then clears them.  ms, counts: host
+ * arrays of 4.  enable = 0 stops recording. */
 chorus_status chorus_timing_enable(chorus_mesh mesh, int enable);
 chorus_status chorus_timing_read(chorus_mesh mesh, void* stream, double* ms, int64_t* counts);
 
@@ -286,10 +287,11 @@ chorus_status chorus_timing_read(chorus_mesh mesh, void* stream, double* ms, int
  * need a residual - for example an application that has handed all device memory to its own pool
  * allocator, or a latency-critical loop that must not call cudaMalloc (which can synchronise the
  * device).  They pass only the state Q and the output R (device, layout above); the scratch (face
- * traces, one-sided viscous face fluxes, gradient record) lives in one fixed 32 MiB device array
+ * traces, one-sided viscous face fluxes, gradient record, common face fluxes) lives in one fixed
+ * 32 MiB device array
  * inside the library, which every GPU that loads the library holds until the process exits.
- *  - Size limit: E * (6 * 9 * N^2 + 12 * N^3) words of the chosen precision must fit in 32 MiB
- *    (FP32 p = 3: up to 5,140 elements; FP64 p = 3: up to 2,570).  Larger meshes return
+ *  - Size limit: E * (6 * 14 * N^2 + 12 * N^3) words of the chosen precision must fit in 32 MiB
+ *    (FP32 p = 3: up to 3,971 elements; FP64 p = 3: up to 1,985).  Larger meshes return
  *    CHORUS_EINVAL before any launch; use chorus_residual with a workspace for them.
  *  - Set-up: the first call on a device looks up the array's device address with that device
  *    current; make that first call before any stream capture.  Call with the mesh's device current.

@@ -8,8 +8,13 @@ computes the two error diagnostics on the host):
      discrete residual of the background is left out, so each run's perturbation evolves under its
      own dynamics and not under its order's hydrostatic truncation error.
   2. Training pairs from snapshots of the p = 5 run up to `train_until`: input the projected state,
-     target P R_5(Q_5) - R_2(P Q_5) (chorus_closure_make_pairs), scaled per variable by the RMS of
-     the training data; Adam on the shuffled pairs.  Snapshots after `train_until` are held out.
+     target (chorus_closure_make_pairs), scaled per variable by the RMS of the training data; Adam on
+     the shuffled pairs.  Snapshots after `train_until` are held out.  Two targets:
+       - "residual" (a priori): P R_5(Q_5) - R_2(P Q_5), the coarse residual's one-step defect;
+       - "rollout" (multi-step, no adjoint of the residual needed): the projected fine state
+         `horizon` steps later minus the plain coarse state after `horizon` steps from the same
+         projected state, divided by horizon * dt - the mean tendency the coarse run misses over
+         that window.
   3. Plain p = 2 and closure-corrected p = 2 runs (the correction also relaxed by factors below one)
      from the projected initial state, compared with the reference at the checkpoints by
        - the relative L2 error of the perturbation, per variable, maximum over variables, and
@@ -93,8 +98,11 @@ class Diagnostics:
 
 
 def evaluate(steps=2000, check_every=100, snap_every=50, train_until=1000, epochs=20, batch=1024, lr=1e-3,
-             seed=11, relax=(1.0, 0.5, 0.25, 0.1)):
-    """relax: factors applied to the trained closure's output (one coarse run each)."""
+             seed=11, relax=(1.0, 0.5, 0.25, 0.1), target="residual", horizon=50):
+    """relax: factors applied to the trained closure's output (one coarse run each).  target:
+    "residual" or "rollout" (horizon steps; a multiple of snap_every)."""
+    if target == "rollout" and horizon % snap_every:
+        raise ValueError("the rollout horizon must be a multiple of snap_every")
     import torch
 
     from chorus_inputs import SHELL_98304_P2, SHELL_98304_P5, cubed_sphere_hex20
@@ -151,6 +159,20 @@ def evaluate(steps=2000, check_every=100, snap_every=50, train_until=1000, epoch
         fine_ms += ev0.elapsed_time(ev1)
         n += stride
     fine_run_s = time.perf_counter() - t0
+
+    # ---- rollout targets: (P Q_5(n + horizon) - coarse^horizon(P Q_5(n))) / (horizon dt), in the slot of
+    # the projected fine residual, with a zero coarse residual (make_pairs forms their difference)
+    if target == "rollout":
+        by_step = {st: qc for st, qc, _, _ in snaps}
+        zero = torch.zeros(cshape, **f32)
+        rolled = []
+        for st, qc, _, _ in snaps:
+            if st + horizon not in by_step:
+                continue
+            q = qc.clone()
+            coarse.mesh.rk_step(coarse.params, FP32_PERT, q, wsc, dt, horizon)
+            rolled.append((st, qc, (by_step[st + horizon] - q) / (horizon * dt), zero))
+        snaps = rolled
 
     # ---- 2. pairs, scales, training
     t0 = time.perf_counter()
@@ -230,7 +252,8 @@ def evaluate(steps=2000, check_every=100, snap_every=50, train_until=1000, epoch
         "l2": {k: v["l2"] for k, v in out.items()},
         "ke_err": {k: v["ke"] for k, v in out.items()},
         "ke_spectrum_ref_final": ke_ref.tolist(),
-        "train": {"pairs": int(Xtr.shape[0]), "epochs": epochs, "batch": batch, "lr": lr,
+        "train": {"target": target, "horizon": horizon if target == "rollout" else 1,
+                  "pairs": int(Xtr.shape[0]), "epochs": epochs, "batch": batch, "lr": lr,
                   "loss_first": losses[0], "loss_last": losses[-1], "held_out_ratio": held,
                   "in_scale": in_scale, "out_scale": out_scale, "train_until": train_until,
                   "snap_every": snap_every},
@@ -251,11 +274,16 @@ def main():
     ap.add_argument("--epochs", type=int, default=20)
     ap.add_argument("--batch", type=int, default=1024)
     ap.add_argument("--lr", type=float, default=1e-3)
+    ap.add_argument("--target", default="residual", choices=["residual", "rollout"])
+    ap.add_argument("--horizon", type=int, default=50)
+    ap.add_argument("--relax", default="1,0.5,0.25,0.1")
     a = ap.parse_args()
     from . import build
 
     build.build()
-    print(json.dumps(evaluate(a.steps, a.check_every, a.snap_every, a.train_until, a.epochs, a.batch, a.lr)))
+    relax = tuple(float(x) for x in a.relax.split(","))
+    print(json.dumps(evaluate(a.steps, a.check_every, a.snap_every, a.train_until, a.epochs, a.batch, a.lr,
+                              relax=relax, target=a.target, horizon=a.horizon)))
 
 
 if __name__ == "__main__":

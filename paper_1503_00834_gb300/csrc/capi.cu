@@ -193,14 +193,19 @@ __global__ void k_d2f(int64_t n, const double* __restrict__ a, float* __restrict
   if (i < n) b[i] = (float)a[i];
 }
 
-// background tables of the perturbation form from the FP64 background state and its traces
-__global__ void k_bg_tables(int64_t E, int N3, int N2, const double* __restrict__ Q0, const double* __restrict__ T,
-                            float* __restrict__ bg, float* __restrict__ bgT) {
+// background tables of the perturbation form from the FP64 background state and its traces (rho0,
+// E0 and the lifted grad rho0 in the tables' point order, bg_point)
+__global__ void k_bg_tables(int64_t E, int N, const double* __restrict__ Q0, const double* __restrict__ T,
+                            const double* __restrict__ grho0, float* __restrict__ bg, float* __restrict__ bgT,
+                            float* __restrict__ grho0_f) {
+  const int N2 = N * N, N3 = N2 * N;
   const int64_t g = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (g < E * N3) {
     const int64_t e = g / N3, pt = g % N3;
-    bg[(e * 2) * N3 + pt] = (float)Q0[(e * 5) * N3 + pt];
-    bg[(e * 2 + 1) * N3 + pt] = (float)Q0[(e * 5 + 4) * N3 + pt];
+    const int bp = bg_point(N, (int)pt);
+    bg[(e * 2) * N3 + bp] = (float)Q0[(e * 5) * N3 + pt];
+    bg[(e * 2 + 1) * N3 + bp] = (float)Q0[(e * 5 + 4) * N3 + pt];
+    for (int n = 0; n < 3; ++n) grho0_f[(e * 3 + n) * N3 + bp] = (float)grho0[(e * 3 + n) * N3 + pt];
   }
   if (g < E * 6 * N2) {
     const int64_t ef = g / N2, t = g % N2;
@@ -418,6 +423,7 @@ void free_mesh(chorus_mesh_s* m) {
   dev_free(m->d_kr32);
   dev_free(m->d_err);
   dev_free(m->d_red);
+  dev_free(m->d_faces);
   delete m;
 }
 
@@ -425,8 +431,9 @@ size_t ws_words(const chorus_mesh_s* m) {
   const size_t N = m->N, E = m->E;
   const size_t N2 = N * N, N3 = N2 * N;
   // stage buffer + two trace buffers + viscous normal-flux traces + two more stage buffers (RK(5,4))
-  // + the gradient record handed from the gradient kernel to the residual kernel
-  return 3 * E * 5 * N3 + 2 * E * 6 * 5 * N2 + E * 6 * 4 * N2 + E * 12 * N3;
+  // + the gradient record handed from the gradient kernel to the residual kernel + the common face
+  // fluxes of every face point
+  return 3 * E * 5 * N3 + 2 * E * 6 * 5 * N2 + E * 6 * 4 * N2 + E * 12 * N3 + E * 6 * 5 * N2;
 }
 
 template <class R>
@@ -438,6 +445,7 @@ struct Ws {
   R* A;
   R* B;
   R* G;
+  R* Fc;
 };
 
 template <class R>
@@ -453,6 +461,7 @@ Ws<R> split_ws(const chorus_mesh_s* m, void* w) {
   r.A = r.Tv + E * 6 * 4 * N2;
   r.B = r.A + E * 5 * N3;
   r.G = r.B + E * 5 * N3;
+  r.Fc = r.G + E * 12 * N3;
   return r;
 }
 
@@ -579,6 +588,21 @@ chorus_status chorus_mesh_create(int64_t n_nodes, const double* node_xyz, int64_
     free_mesh(m);
     return CHORUS_ENOMEM;
   }
+  // the face kernel's work list: interior faces from their lower-numbered element, then wall faces
+  std::vector<int2> faces;
+  faces.reserve((size_t)(m->host.n_interior_faces + m->host.n_wall_faces));
+  for (size_t e = 0; e < E; ++e)
+    for (int F = 0; F < 6; ++F)
+      if (m->host.nbr[e * 6 + F] > (int)e) faces.push_back(make_int2((int)e, F));
+  m->n_ifaces = (int)faces.size();
+  for (size_t e = 0; e < E; ++e)
+    for (int F = 0; F < 6; ++F)
+      if (m->host.nbr[e * 6 + F] < 0) faces.push_back(make_int2((int)e, F));
+  m->n_wfaces = (int)faces.size() - m->n_ifaces;
+  if (!faces.empty() && dev_alloc(&m->d_faces, faces.size()) != cudaSuccess) {
+    free_mesh(m);
+    return CHORUS_ENOMEM;
+  }
   cudaError_t ce = cudaSuccess;
   auto up = [&](void* d, const void* h, size_t bytes) {
     if (ce == cudaSuccess) ce = cudaMemcpyAsync(d, h, bytes, cudaMemcpyHostToDevice, st);
@@ -590,6 +614,7 @@ chorus_status chorus_mesh_create(int64_t n_nodes, const double* node_xyz, int64_
   up(m->d_invJ64, invJ.data(), nP * sizeof(double));
   up(m->d_x64, m->host.x.data(), 3 * nP * sizeof(double));
   up(m->d_wJ, wJ.data(), nP * sizeof(double));
+  if (!faces.empty()) up(m->d_faces, faces.data(), faces.size() * sizeof(int2));
   for (size_t i = 0; i < nS; ++i) f32[i] = (float)m->host.Sf[i];
   up(m->d_Sf32, f32.data(), nS * sizeof(float));
   for (size_t i = 0; i < nP; ++i) f32[i] = (float)invJ[i];
@@ -649,10 +674,10 @@ chorus_status prepare_background(chorus_mesh_s* m, const chorus_params* P, int64
     free_background(m);
     return CHORUS_ENOMEM;
   }
-  double *T = nullptr, *Tv = nullptr, *R0 = nullptr, *gr = nullptr, *tab = nullptr, *G = nullptr;
+  double *T = nullptr, *Tv = nullptr, *R0 = nullptr, *gr = nullptr, *tab = nullptr, *G = nullptr, *Fc = nullptr;
   if (dev_alloc(&T, nT) || dev_alloc(&Tv, E * 6 * 4 * N2) || dev_alloc(&R0, 5 * nP) || dev_alloc(&gr, 3 * nP) ||
-      dev_alloc(&G, (size_t)kG * nP) || (rho_tab && dev_alloc(&tab, 2 * (size_t)n_tab))) {
-    dev_free(T); dev_free(Tv); dev_free(R0); dev_free(gr); dev_free(tab); dev_free(G);
+      dev_alloc(&G, (size_t)kG * nP) || dev_alloc(&Fc, nT) || (rho_tab && dev_alloc(&tab, 2 * (size_t)n_tab))) {
+    dev_free(T); dev_free(Tv); dev_free(R0); dev_free(gr); dev_free(tab); dev_free(G); dev_free(Fc);
     free_background(m);
     return CHORUS_ENOMEM;
   }
@@ -673,18 +698,19 @@ chorus_status prepare_background(chorus_mesh_s* m, const chorus_params* P, int64
     ce = cudaGetLastError();
   }
   if (ce == cudaSuccess) ce = m->L.trace64(ma, m->ops64, m->d_Q0, T, st);
-  if (ce == cudaSuccess) ce = m->L.grad64(ma, m->ops64, ph, m->d_Q0, T, Tv, gr, G, m->d_err, st);
+  if (ce == cudaSuccess) ce = m->L.grad64(ma, m->ops64, ph, m->d_Q0, T, Tv, gr, G, Fc, m->d_err, st);
+  if (ce == cudaSuccess) ce = m->L.face64(ma, ph, m->d_faces, m->n_ifaces, m->n_wfaces, T, Tv, Fc, st);
   if (ce == cudaSuccess)
-    ce = m->L.resid64(ma, m->ops64, ph, m->d_Q0, T, Tv, G, R0, nullptr, RkCoef<double>{}, 0.0, kModeResidual,
+    ce = m->L.resid64(ma, m->ops64, ph, m->d_Q0, T, Tv, G, Fc, R0, nullptr, RkCoef<double>{}, 0.0, kModeResidual,
                       m->d_err, st);
   if (ce == cudaSuccess) {
     k_d2f<<<grid1(5 * nP), 256, 0, st>>>((int64_t)(5 * nP), R0, m->d_R0);
-    k_d2f<<<grid1(3 * nP), 256, 0, st>>>((int64_t)(3 * nP), gr, m->d_grho0);
-    k_bg_tables<<<grid1(std::max(nP, E * 6 * N2)), 256, 0, st>>>((int64_t)E, N3, N2, m->d_Q0, T, m->d_bg, m->d_bgT);
+    k_bg_tables<<<grid1(std::max(nP, E * 6 * N2)), 256, 0, st>>>((int64_t)E, N, m->d_Q0, T, gr, m->d_bg, m->d_bgT,
+                                                                 m->d_grho0);
     ce = cudaGetLastError();
   }
   if (ce == cudaSuccess) ce = cudaStreamSynchronize(st);
-  dev_free(T); dev_free(Tv); dev_free(R0); dev_free(gr); dev_free(tab); dev_free(G);
+  dev_free(T); dev_free(Tv); dev_free(R0); dev_free(gr); dev_free(tab); dev_free(G); dev_free(Fc);
   if (ce != cudaSuccess) {
     free_background(m);
     return CHORUS_ECUDA;
@@ -809,8 +835,9 @@ chorus_status chorus_residual(chorus_mesh m, const chorus_params* P, chorus_prec
     Ws<double> w = split_ws<double>(m, workspace);
     CHK(timed(m, 0, st, [&] { return m->L.trace64(ma, m->ops64, (const double*)Q, w.Ta, st); }));
     CHK(timed(m, 1, st, [&] {
-      return m->L.grad64(ma, m->ops64, ph, (const double*)Q, w.Ta, w.Tv, nullptr, w.G, m->d_err, st);
+      return m->L.grad64(ma, m->ops64, ph, (const double*)Q, w.Ta, w.Tv, nullptr, w.G, w.Fc, m->d_err, st);
     }));
+    CHK(timed(m, 3, st, [&] { return m->L.face64(ma, ph, m->d_faces, m->n_ifaces, m->n_wfaces, w.Ta, w.Tv, w.Fc, st); }));
     RkCoef<double> rc{};
     if (m->closure) {
       if (!m->prepared) return CHORUS_EINVAL;  // the network reads q' = Q - Q0
@@ -818,7 +845,7 @@ chorus_status chorus_residual(chorus_mesh m, const chorus_params* P, chorus_prec
       rc.radd = (const double*)m->closure_buf;
     }
     CHK(timed(m, 2, st, [&] {
-      return m->L.resid64(ma, m->ops64, ph, (const double*)Q, w.Ta, w.Tv, w.G, (double*)R, nullptr, rc, 0.0,
+      return m->L.resid64(ma, m->ops64, ph, (const double*)Q, w.Ta, w.Tv, w.G, w.Fc, (double*)R, nullptr, rc, 0.0,
                           kModeResidual, m->d_err, st);
     }));
     return CHORUS_OK;
@@ -832,14 +859,17 @@ chorus_status chorus_residual(chorus_mesh m, const chorus_params* P, chorus_prec
   Ws<float> w = split_ws<float>(m, workspace);
   const BgArg bg = bg_arg(m);
   CHK(timed(m, 0, st, [&] { return m->L.trace32(ma, m->ops32, (const float*)Q, w.Ta, st); }));
-  CHK(timed(m, 1, st, [&] { return m->L.grad32(ma, m->ops32, ph, bg, (const float*)Q, w.Ta, w.Tv, w.G, m->d_err, st); }));
+  CHK(timed(m, 1, st, [&] {
+    return m->L.grad32(ma, m->ops32, ph, bg, (const float*)Q, w.Ta, w.Tv, w.G, w.Fc, m->d_err, st);
+  }));
+  CHK(timed(m, 3, st, [&] { return m->L.face32(ma, ph, bg, m->d_faces, m->n_ifaces, m->n_wfaces, w.Ta, w.Tv, w.Fc, st); }));
   RkCoef<float> rc{};
   if (m->closure) {
     CHK(mlp_elements_tc(1, m->closure, Q, nullptr, m->closure_buf, m->E, 0, m->d_err, st));
     rc.radd = (const float*)m->closure_buf;
   }
   CHK(timed(m, 2, st, [&] {
-    return m->L.resid32(ma, m->ops32, ph, bg, (const float*)Q, w.Ta, w.Tv, w.G, (float*)R, nullptr, rc, 0.0f,
+    return m->L.resid32(ma, m->ops32, ph, bg, (const float*)Q, w.Ta, w.Tv, w.G, w.Fc, (float*)R, nullptr, rc, 0.0f,
                         kModeResidual, m->d_err, st);
   }));
   return CHORUS_OK;
@@ -877,9 +907,9 @@ const std::vector<Stage>& stages_of(int scheme) {
   return scheme == 1 ? rk54 : rk3;
 }
 
-template <class R, class Grad, class Resid, class Trace>
+template <class R, class Grad, class Face, class Resid, class Trace>
 chorus_status run_rk(chorus_mesh_s* m, R* u, const Ws<R>& w, double dt, int64_t n_steps, int scheme, cudaStream_t st,
-                     Grad grad, Resid resid, Trace trace) {
+                     Grad grad, Face face, Resid resid, Trace trace) {
   R* buf[4] = {u, w.s, w.A, w.B};
   R *Tc = w.Ta, *Tn = w.Tb;
   CHK(timed(m, 0, st, [&] { return trace(u, Tc); }));
@@ -894,6 +924,7 @@ chorus_status run_rk(chorus_mesh_s* m, R* u, const Ws<R>& w, double dt, int64_t 
         c.radd = (const R*)m->closure_buf;
       }
       CHK(timed(m, 1, st, [&] { return grad(buf[g.src], Tc); }));
+      CHK(timed(m, 3, st, [&] { return face(Tc); }));
       CHK(timed(m, 2, st, [&] { return resid(buf[g.src], Tc, buf[g.dst], Tn, c); }));
       std::swap(Tc, Tn);
     }
@@ -921,10 +952,11 @@ chorus_status chorus_rk_step_scheme(chorus_mesh m, const chorus_params* P, choru
     return run_rk<double>(
         m, (double*)Q, w, dt, n_steps, scheme, st,
         [&](const double* q, const double* T) {
-          return m->L.grad64(ma, m->ops64, ph, q, T, w.Tv, nullptr, w.G, m->d_err, st);
+          return m->L.grad64(ma, m->ops64, ph, q, T, w.Tv, nullptr, w.G, w.Fc, m->d_err, st);
         },
+        [&](const double* T) { return m->L.face64(ma, ph, m->d_faces, m->n_ifaces, m->n_wfaces, T, w.Tv, w.Fc, st); },
         [&](const double* q, const double* T, double* dst, double* Tn, const RkCoef<double>& c) {
-          return m->L.resid64(ma, m->ops64, ph, q, T, w.Tv, w.G, dst, Tn, c, dt, kModeRK, m->d_err, st);
+          return m->L.resid64(ma, m->ops64, ph, q, T, w.Tv, w.G, w.Fc, dst, Tn, c, dt, kModeRK, m->d_err, st);
         },
         [&](const double* q, double* T) { return m->L.trace64(ma, m->ops64, q, T, st); });
   }
@@ -938,9 +970,12 @@ chorus_status chorus_rk_step_scheme(chorus_mesh m, const chorus_params* P, choru
   Ws<float> w = split_ws<float>(m, workspace);
   return run_rk<float>(
       m, (float*)Q, w, dt, n_steps, scheme, st,
-      [&](const float* q, const float* T) { return m->L.grad32(ma, m->ops32, ph, bg, q, T, w.Tv, w.G, m->d_err, st); },
+      [&](const float* q, const float* T) {
+        return m->L.grad32(ma, m->ops32, ph, bg, q, T, w.Tv, w.G, w.Fc, m->d_err, st);
+      },
+      [&](const float* T) { return m->L.face32(ma, ph, bg, m->d_faces, m->n_ifaces, m->n_wfaces, T, w.Tv, w.Fc, st); },
       [&](const float* q, const float* T, float* dst, float* Tn, const RkCoef<float>& c) {
-        return m->L.resid32(ma, m->ops32, ph, bg, q, T, w.Tv, w.G, dst, Tn, c, (float)dt, kModeRK, m->d_err, st);
+        return m->L.resid32(ma, m->ops32, ph, bg, q, T, w.Tv, w.G, w.Fc, dst, Tn, c, (float)dt, kModeRK, m->d_err, st);
       },
       [&](const float* q, float* T) { return m->L.trace32(ma, m->ops32, q, T, st); });
 }
@@ -1176,7 +1211,7 @@ chorus_status chorus_timing_enable(chorus_mesh m, int enable) {
 chorus_status chorus_timing_read(chorus_mesh m, void* stream, double* ms, int64_t* counts) {
   if (!m || !ms || !counts) return CHORUS_EINVAL;
   CHK(cudaStreamSynchronize((cudaStream_t)stream));
-  for (int c = 0; c < 3; ++c) {
+  for (int c = 0; c < 4; ++c) {
     ms[c] = 0.0;
     counts[c] = 0;
   }
@@ -1184,7 +1219,7 @@ chorus_status chorus_timing_read(chorus_mesh m, void* stream, double* ms, int64_
   for (auto& r : m->recs) {
     float t = 0.f;
     if (e == cudaSuccess) e = cudaEventElapsedTime(&t, r.a, r.b);
-    if (r.cls >= 0 && r.cls < 3) {
+    if (r.cls >= 0 && r.cls < 4) {
       ms[r.cls] += t;
       counts[r.cls] += 1;
     }
@@ -1316,7 +1351,7 @@ extern "C" chorus_status chorus_residual_noalloc(chorus_mesh m, const chorus_par
   const size_t word = prec == CHORUS_FP64 ? sizeof(double) : sizeof(float);
   const size_t N3 = N2 * (size_t)m->N;
   const size_t nT = E * 6 * 5 * N2, nTv = E * 6 * 4 * N2, nG = E * kG * N3;
-  if ((nT + nTv + nG) * word > kNoAllocScratchBytes) return CHORUS_EINVAL;  // mesh too large for the scratch
+  if ((2 * nT + nTv + nG) * word > kNoAllocScratchBytes) return CHORUS_EINVAL;  // mesh too large for the scratch
   if (prec == CHORUS_FP32_PERT && (!m->prepared || !same_params(m->prep, *P))) return CHORUS_EINVAL;
   // the attached closure's output buffer was allocated by chorus_closure_attach; FP64 reads Q0
   if (m->closure && prec == CHORUS_FP64 && !m->prepared) return CHORUS_EINVAL;
@@ -1334,14 +1369,16 @@ extern "C" chorus_status chorus_residual_noalloc(chorus_mesh m, const chorus_par
     double* T = (double*)scratch;
     double* Tv = T + nT;
     double* G = Tv + nTv;
+    double* Fc = G + nG;
     RkCoef<double> rc{};
     if (m->closure) {
       CHK(mlp_elements_tc(0, m->closure, Q, m->d_Q0, m->closure_buf, m->E, 0, m->d_err, st));
       rc.radd = (const double*)m->closure_buf;
     }
     CHK(m->L.trace64(ma, m->ops64, (const double*)Q, T, st));
-    CHK(m->L.grad64(ma, m->ops64, ph, (const double*)Q, T, Tv, nullptr, G, m->d_err, st));
-    CHK(m->L.resid64(ma, m->ops64, ph, (const double*)Q, T, Tv, G, (double*)R, nullptr, rc, 0.0, kModeResidual,
+    CHK(m->L.grad64(ma, m->ops64, ph, (const double*)Q, T, Tv, nullptr, G, Fc, m->d_err, st));
+    CHK(m->L.face64(ma, ph, m->d_faces, m->n_ifaces, m->n_wfaces, T, Tv, Fc, st));
+    CHK(m->L.resid64(ma, m->ops64, ph, (const double*)Q, T, Tv, G, Fc, (double*)R, nullptr, rc, 0.0, kModeResidual,
                      m->d_err, st));
     return CHORUS_OK;
   }
@@ -1351,14 +1388,16 @@ extern "C" chorus_status chorus_residual_noalloc(chorus_mesh m, const chorus_par
   float* T = (float*)scratch;
   float* Tv = T + nT;
   float* G = Tv + nTv;
+  float* Fc = G + nG;
   RkCoef<float> rc{};
   if (m->closure) {
     CHK(mlp_elements_tc(1, m->closure, Q, nullptr, m->closure_buf, m->E, 0, m->d_err, st));
     rc.radd = (const float*)m->closure_buf;
   }
   CHK(m->L.trace32(ma, m->ops32, (const float*)Q, T, st));
-  CHK(m->L.grad32(ma, m->ops32, ph, bg, (const float*)Q, T, Tv, G, m->d_err, st));
-  CHK(m->L.resid32(ma, m->ops32, ph, bg, (const float*)Q, T, Tv, G, (float*)R, nullptr, rc, 0.0f, kModeResidual,
+  CHK(m->L.grad32(ma, m->ops32, ph, bg, (const float*)Q, T, Tv, G, Fc, m->d_err, st));
+  CHK(m->L.face32(ma, ph, bg, m->d_faces, m->n_ifaces, m->n_wfaces, T, Tv, Fc, st));
+  CHK(m->L.resid32(ma, m->ops32, ph, bg, (const float*)Q, T, Tv, G, Fc, (float*)R, nullptr, rc, 0.0f, kModeResidual,
                    m->d_err, st));
   return CHORUS_OK;
 }

@@ -51,6 +51,18 @@ struct BgArg {
   const float* R0;     // [E][5][N^3]     FP64 residual of the background, rounded (null: left out)
 };
 
+// Point order of the FP32 background tables rho0, E0 and the lifted grad rho0: at N = 4 they are
+// stored in the kernels' XOR-swizzled shared-memory order (point (i,j,k) at i + 4((j^k)&3) + 16k),
+// so that the bulk copies land them conflict-free for the line sweeps of every direction; at other
+// orders in the state's linear order i + N j + N^2 k.
+constexpr bool kBgSwizzle = true;
+__host__ __device__ inline constexpr bool bg_swizzle(int N) { return kBgSwizzle && N == 4; }
+__host__ __device__ inline int bg_point(int N, int pt) {
+  if (!bg_swizzle(N)) return pt;
+  const int i = pt % 4, j = (pt / 4) % 4, k = pt / 16;
+  return i + 4 * ((j ^ k) & 3) + 16 * k;
+}
+
 enum ResidMode { kModeResidual = 0, kModeRK = 1 };
 
 // Stage combination of the RK update fused into the residual kernel:
@@ -71,18 +83,25 @@ struct RkCoef {
 struct LaunchSet {
   cudaError_t (*trace64)(const MeshArg<double>&, const OpsArg<double>&, const double* q, double* T, cudaStream_t);
   // G: gradient record [E][12][N^3] written by grad (when non-null) and read by resid (required:
-  // resid returns cudaErrorInvalidValue without it)
+  // resid returns cudaErrorInvalidValue without it).  Fc: common face fluxes F~ [E][6][5][N^2], written
+  // by face (interior and wall faces) and read by resid (required).
   cudaError_t (*grad64)(const MeshArg<double>&, const OpsArg<double>&, const PhysArg<double>&, const double* q,
-                        const double* T, double* Tv, double* grad_rho_out, double* G, unsigned* err, cudaStream_t);
+                        const double* T, double* Tv, double* grad_rho_out, double* G, double* Fc, unsigned* err,
+                        cudaStream_t);
+  // faces: n_faces interior faces (from their lower element), then n_walls wall faces
+  cudaError_t (*face64)(const MeshArg<double>&, const PhysArg<double>&, const int2* faces, int n_faces, int n_walls,
+                        const double* T, const double* Tv, double* Fc, cudaStream_t);
   cudaError_t (*resid64)(const MeshArg<double>&, const OpsArg<double>&, const PhysArg<double>&, const double* q,
-                         const double* T, const double* Tv, const double* G, double* out, double* T_out,
-                         const RkCoef<double>& rk, double dt, int mode, unsigned* err, cudaStream_t);
+                         const double* T, const double* Tv, const double* G, const double* Fc, double* out,
+                         double* T_out, const RkCoef<double>& rk, double dt, int mode, unsigned* err, cudaStream_t);
   cudaError_t (*trace32)(const MeshArg<float>&, const OpsArg<float>&, const float* q, float* T, cudaStream_t);
   cudaError_t (*grad32)(const MeshArg<float>&, const OpsArg<float>&, const PhysArg<float>&, const BgArg&,
-                        const float* q, const float* T, float* Tv, float* G, unsigned* err, cudaStream_t);
+                        const float* q, const float* T, float* Tv, float* G, float* Fc, unsigned* err, cudaStream_t);
+  cudaError_t (*face32)(const MeshArg<float>&, const PhysArg<float>&, const BgArg&, const int2* faces, int n_faces,
+                        int n_walls, const float* T, const float* Tv, float* Fc, cudaStream_t);
   cudaError_t (*resid32)(const MeshArg<float>&, const OpsArg<float>&, const PhysArg<float>&, const BgArg&,
-                         const float* q, const float* T, const float* Tv, const float* G, float* out, float* T_out,
-                         const RkCoef<float>& rk, float dt, int mode, unsigned* err, cudaStream_t);
+                         const float* q, const float* T, const float* Tv, const float* G, const float* Fc, float* out,
+                         float* T_out, const RkCoef<float>& rk, float dt, int mode, unsigned* err, cudaStream_t);
   int epb32;  // elements per CTA of the FP32 kernels
 };
 

@@ -23,19 +23,31 @@ struct Inst {
   }
   static cudaError_t grad64(const MeshArg<double>& m, const OpsArg<double>& ops, const PhysArg<double>& ph,
                             const double* q, const double* T, double* Tv, double* grad_rho_out, double* G,
-                            unsigned* err, cudaStream_t st) {
+                            double* Fc, unsigned* err, cudaStream_t st) {
     KArgs<double> A{};
     A.m = m; A.ops = ops; A.ph = ph; A.q = q; A.T = T; A.Tv_out = Tv; A.grad_rho_out = grad_rho_out; A.err = err;
-    A.G_out = G;
+    A.G_out = G; A.Fc_out = Fc;
     return L64::grad(A, st);
   }
   static cudaError_t grad32(const MeshArg<float>& m, const OpsArg<float>& ops, const PhysArg<float>& ph,
-                            const BgArg& bg, const float* q, const float* T, float* Tv, float* G, unsigned* err,
-                            cudaStream_t st) {
+                            const BgArg& bg, const float* q, const float* T, float* Tv, float* G, float* Fc,
+                            unsigned* err, cudaStream_t st) {
     KArgs<float> A{};
     A.m = m; A.ops = ops; A.ph = ph; A.bg = bg; A.q = q; A.T = T; A.Tv_out = Tv; A.err = err;
-    A.G_out = G;
+    A.G_out = G; A.Fc_out = Fc;
     return L32::grad(A, st);
+  }
+  static cudaError_t face64(const MeshArg<double>& m, const PhysArg<double>& ph, const int2* faces, int nf, int nw,
+                            const double* T, const double* Tv, double* Fc, cudaStream_t st) {
+    KArgs<double> A{};
+    A.m = m; A.ph = ph; A.T = T; A.Tv = Tv; A.Fc_out = Fc;
+    return L64::face(A, faces, nf, nw, st);
+  }
+  static cudaError_t face32(const MeshArg<float>& m, const PhysArg<float>& ph, const BgArg& bg, const int2* faces,
+                            int nf, int nw, const float* T, const float* Tv, float* Fc, cudaStream_t st) {
+    KArgs<float> A{};
+    A.m = m; A.ph = ph; A.bg = bg; A.T = T; A.Tv = Tv; A.Fc_out = Fc;
+    return L32::face(A, faces, nf, nw, st);
   }
   template <class R>
   static void set_rk(KArgs<R>& A, const RkCoef<R>& rk) {
@@ -43,27 +55,30 @@ struct Inst {
     A.un2 = rk.un2; A.out2 = rk.out2; A.a2 = rk.a2; A.b2 = rk.b2; A.c2 = rk.c2; A.radd = rk.radd;
   }
   static cudaError_t resid64(const MeshArg<double>& m, const OpsArg<double>& ops, const PhysArg<double>& ph,
-                             const double* q, const double* T, const double* Tv, const double* G, double* out,
-                             double* T_out, const RkCoef<double>& rk, double dt, int mode, unsigned* err,
+                             const double* q, const double* T, const double* Tv, const double* G, const double* Fc,
+                             double* out, double* T_out, const RkCoef<double>& rk, double dt, int mode, unsigned* err,
                              cudaStream_t st) {
     KArgs<double> A{};
     A.m = m; A.ops = ops; A.ph = ph; A.q = q; A.T = T; A.Tv = Tv; A.out = out; A.T_out = T_out; A.G_in = G;
+    A.Fc = Fc;
     set_rk(A, rk);
     A.dt = dt; A.err = err;
     return mode == kModeRK ? L64::template resid<kModeRK>(A, st) : L64::template resid<kModeResidual>(A, st);
   }
   static cudaError_t resid32(const MeshArg<float>& m, const OpsArg<float>& ops, const PhysArg<float>& ph,
                              const BgArg& bg, const float* q, const float* T, const float* Tv, const float* G,
-                             float* out, float* T_out, const RkCoef<float>& rk, float dt, int mode, unsigned* err,
-                             cudaStream_t st) {
+                             const float* Fc, float* out, float* T_out, const RkCoef<float>& rk, float dt, int mode,
+                             unsigned* err, cudaStream_t st) {
     KArgs<float> A{};
     A.m = m; A.ops = ops; A.ph = ph; A.bg = bg; A.q = q; A.T = T; A.Tv = Tv; A.out = out; A.T_out = T_out;
-    A.G_in = G;
+    A.G_in = G; A.Fc = Fc;
     set_rk(A, rk);
     A.dt = dt; A.err = err;
     return mode == kModeRK ? L32R::template resid<kModeRK>(A, st) : L32R::template resid<kModeResidual>(A, st);
   }
-  static LaunchSet set() { return LaunchSet{trace64, grad64, resid64, trace32, grad32, resid32, EPB32}; }
+  static LaunchSet set() {
+    return LaunchSet{trace64, grad64, face64, resid64, trace32, grad32, face32, resid32, EPB32};
+  }
 };
 
 }  // namespace chorus

@@ -32,6 +32,9 @@ struct chorus_mesh_s {
   float* d_invJ32 = nullptr;
   float* d_x32 = nullptr;
   unsigned* d_err = nullptr;
+  // face list (element, local face): the interior faces from their lower element, then the wall faces
+  int2* d_faces = nullptr;
+  int n_ifaces = 0, n_wfaces = 0;
   // prepared background
   bool prepared = false;
   chorus_params prep{};

@@ -13,6 +13,8 @@
 // zeta-line accesses are conflict free.  Neighbour face data are gathered from global memory
 // straight into registers when a sweep needs them.
 #pragma once
+#include <type_traits>
+
 #include "sd_device.cuh"
 
 namespace chorus {
@@ -105,6 +107,13 @@ constexpr bool kStageMetricsN4 = true;
 template <int N, class R>
 __host__ __device__ constexpr bool stage_metrics() { return sizeof(R) == 4 && N == 4 && kStageMetricsN4; }
 
+// Face-kernel mode: the common flux of every interior face point is computed once by k_face (Rusanov
+// + averaged viscous, from both sides' traces) and of every wall face point by the lifting kernel
+// (which holds the face gradients), both written as F~ in each element's own face numbering; the
+// residual kernel's sweeps then evaluate fluxes at the interior flux points only and take the two
+// end points' F~ from that array (one coalesced read per face) instead of gathering neighbour data.
+constexpr bool kFaceKernel = true;
+
 // Lifting order: false = directions 0, 1, 2 and a separate pass that forms the gradient record;
 // true = directions 1, 2, 0 with the record formed in the last sweep.
 constexpr bool kLiftFused = true;
@@ -116,6 +125,15 @@ constexpr bool kLiftFused = true;
 constexpr bool kLiftRaw = true;
 template <int N, class R>
 __host__ __device__ constexpr bool lift_raw() { return kLiftRaw && kLiftFused && sizeof(R) == 4 && N == 4; }
+// Direction order of the raw-derivative lifting: xi, eta, zeta (the xi sweep stores its raw slot as
+// 16-byte vectors, conflict-free in the swizzled layout, and the record is formed in the zeta sweep,
+// whose scalar accesses are conflict-free in both the swizzled and the linear layout); otherwise
+// eta, zeta, xi as in the accumulated lifting.
+constexpr bool kLiftXiFirst = true;
+template <int N, class R>
+__host__ __device__ constexpr int lift_dir_at(int k) {
+  return (lift_raw<N, R>() && kLiftXiFirst) ? k : (k == 0 ? 1 : k == 1 ? 2 : 0);
+}
 
 // Whether the lifting kernel writes the gradient record with bulk stores from shared memory (timed
 // per order: 1-4 % faster at N = 3, 4, 6, 3 % slower at N = 5).
@@ -183,6 +201,33 @@ __device__ __forceinline__ void load_line_lin(const R* __restrict__ base, int ln
   }
 }
 
+// Load the N values of one background table component (rho0, E0 or a component of the lifted
+// grad rho0) along line ln of direction D, in the tables' point order (bg_point).
+template <int N, int D, class R>
+__device__ __forceinline__ void load_line_bg(const R* __restrict__ base, int ln, R out[N]) {
+  if constexpr (bg_swizzle(N) && sizeof(R) == 4) {
+    if constexpr (D == 0) {
+      const float4 v = *reinterpret_cast<const float4*>(base + line_sidx<N, 0, R>(ln, 0));
+      out[0] = v.x;
+      out[1] = v.y;
+      out[2] = v.z;
+      out[3] = v.w;
+    } else {
+#pragma unroll
+      for (int s = 0; s < N; ++s) out[s] = base[line_sidx<N, D, R>(ln, s)];
+    }
+  } else {
+    load_line_lin<N, D>(base, ln, out);
+  }
+}
+
+// Index of position s along line ln of direction D in the background tables' point order.
+template <int N, int D, class R>
+__device__ __forceinline__ int line_bg(int ln, int s) {
+  if constexpr (bg_swizzle(N) && sizeof(R) == 4) return line_sidx<N, D, R>(ln, s);
+  else return line_pt<N, D>(ln, s);
+}
+
 // Load the kG components of the gradient record along line ln of direction D from the shared array.
 template <int N, int D, class R>
 __device__ __forceinline__ void load_grad_lines(const R* sg, int ln, R (&gv)[kG][N]) {
@@ -230,6 +275,8 @@ struct KArgs {
   R* out2;
   R a2, b2, c2;
   const R* radd;       // optional additive residual correction [E][5][N3]
+  R* Fc_out;           // grad kernel output (face-kernel mode): wall common fluxes F~ [E][6][5][N2]
+  const R* Fc;         // resid kernel input (face-kernel mode): common fluxes F~ of every face point
   unsigned* err;
 };
 
@@ -363,7 +410,7 @@ __device__ __forceinline__ void flux_prefetch(const KArgs<R>& A, int e, int ln, 
 #pragma unroll
     for (int n = 0; n < 3; ++n) p.s3b[n] = __ldg(Sl + (n * (N + 1) + flux_order<N, EF>(1)) * N2 + ln);
   }
-  if (flux_nb_mode<N>() == 1 || flux_nb_mode<N>() == 2) {
+  if (!kFaceKernel && (flux_nb_mode<N>() == 1 || flux_nb_mode<N>() == 2)) {
     p.nbi[0] = nb_index<N>(A, e, 2 * D, ln);
     p.nbi[1] = nb_index<N>(A, e, 2 * D + 1, ln);
   }
@@ -489,8 +536,8 @@ __device__ __forceinline__ void lift_dir(const KArgs<R>& A, R* sm, int el, int l
   for (int v = 0; v < 5; ++v) load_line_lin<N, D>(sq + v * N3, ln, qv[v]);
   R r0[N], E0l[N];
   if (PERT) {
-    load_line_lin<N, D>(sbg, ln, r0);
-    load_line_lin<N, D>(sbg + N3, ln, E0l);
+    load_line_bg<N, D>(sbg, ln, r0);
+    load_line_bg<N, D>(sbg + N3, ln, E0l);
   }
   const auto& S = pre.S;
 
@@ -537,11 +584,15 @@ __device__ __forceinline__ void lift_dir(const KArgs<R>& A, R* sm, int el, int l
       dq[4][side] = Ec - qe[4];
     }
   }
+  // xi sweep at N = 4 (FP32, raw lifting, not last): the raw slot leaves as one 16-byte store per
+  // component, the line's four points being contiguous in the swizzled layout
+  constexpr bool RAWVEC = lift_raw<N, R>() && !LAST && D == 0;
+  R rawv[RAWVEC ? 8 : 1][RAWVEC ? N : 1];
   R g0[LAST && PERT ? 3 : 1][N];
   if constexpr (LAST && PERT) {
     const R* sgr0 = sm + L::oGR0 + el * L::SGR0;
 #pragma unroll
-    for (int n = 0; n < 3; ++n) load_line_lin<N, D>(sgr0 + n * N3, ln, g0[n]);
+    for (int n = 0; n < 3; ++n) load_line_bg<N, D>(sgr0 + n * N3, ln, g0[n]);
   }
 #pragma unroll
   for (int i = 0; i < N; ++i) {
@@ -574,7 +625,12 @@ __device__ __forceinline__ void lift_dir(const KArgs<R>& A, R* sm, int el, int l
         }
       }
     }
-    if constexpr (RAW && !LAST) {
+    if constexpr (RAW && !LAST && RAWVEC) {
+#pragma unroll
+      for (int v = 0; v < 5; ++v) rawv[v][i] = dvv[v];
+#pragma unroll
+      for (int n = 0; n < 3; ++n) rawv[5 + n][i] = gx[n];
+    } else if constexpr (RAW && !LAST) {
       // slot 0 (first sweep) or 1: the five derivatives, then grad xi_D
       constexpr int o = FIRST ? 0 : 8;
 #pragma unroll
@@ -609,6 +665,13 @@ __device__ __forceinline__ void lift_dir(const KArgs<R>& A, R* sm, int el, int l
       for (int c = 0; c < kG; ++c) sg[c * N3 + si] = g[c];
     }
   }
+  if constexpr (RAWVEC) {
+    constexpr int o = FIRST ? 0 : 8;
+    const int s0 = line_sidx<N, 0, R>(ln, 0);
+#pragma unroll
+    for (int c = 0; c < 8; ++c)
+      *reinterpret_cast<float4*>(sg + (o + c) * N3 + s0) = make_float4(rawv[c][0], rawv[c][1], rawv[c][2], rawv[c][3]);
+  }
 }
 
 // Lifting of every element of the CTA; afterwards the first kG component arrays of the gradient
@@ -621,18 +684,19 @@ __device__ __forceinline__ void lift_all(const KArgs<R>& A, R* sm, int el, int l
   using L = Layout<N, PERT, R, EPB>;
   constexpr int N3 = N * N * N;
   if constexpr (kLiftFused) {
-    // directions 1, 2, then 0, which also forms the record (see lift_dir)
+    // three directions (lift_dir_at), the last of which also forms the record (see lift_dir)
+    constexpr int d0 = lift_dir_at<N, R>(0), d1 = lift_dir_at<N, R>(1), d2 = lift_dir_at<N, R>(2);
     if (active) {
-      lift_dir<N, PERT, R, EPB, 1, true, false>(A, sm, el, ln, e, pre);
-      lift_prefetch<N, PERT, R, 2>(A, e, ln, pre);
+      lift_dir<N, PERT, R, EPB, d0, true, false>(A, sm, el, ln, e, pre);
+      lift_prefetch<N, PERT, R, d1>(A, e, ln, pre);
     }
     __syncthreads();
     if (active) {
-      lift_dir<N, PERT, R, EPB, 2, false, false>(A, sm, el, ln, e, pre);
-      lift_prefetch<N, PERT, R, 0>(A, e, ln, pre);
+      lift_dir<N, PERT, R, EPB, d1, false, false>(A, sm, el, ln, e, pre);
+      lift_prefetch<N, PERT, R, d2>(A, e, ln, pre);
     }
     __syncthreads();
-    if (active) lift_dir<N, PERT, R, EPB, 0, false, true>(A, sm, el, ln, e, pre);
+    if (active) lift_dir<N, PERT, R, EPB, d2, false, true>(A, sm, el, ln, e, pre);
     if (grad_bulk_store<N>()) fence_async_smem();  // the record may leave by bulk store after the barrier
     __syncthreads();
     return;
@@ -658,10 +722,10 @@ __device__ __forceinline__ void lift_all(const KArgs<R>& A, R* sm, int el, int l
 #pragma unroll
     for (int v = 0; v < 5; ++v) load_line_lin<N, 0>(sq + v * N3, ln, qv[v]);
     if (PERT) {
-      load_line_lin<N, 0>(sbg, ln, r0);
-      load_line_lin<N, 0>(sbg + N3, ln, E0l);
+      load_line_bg<N, 0>(sbg, ln, r0);
+      load_line_bg<N, 0>(sbg + N3, ln, E0l);
 #pragma unroll
-      for (int n = 0; n < 3; ++n) load_line_lin<N, 0>(sgr0 + n * N3, ln, g0[n]);
+      for (int n = 0; n < 3; ++n) load_line_bg<N, 0>(sgr0 + n * N3, ln, g0[n]);
     }
 #pragma unroll
     for (int i = 0; i < N; ++i) {
@@ -694,10 +758,49 @@ struct FluxPointData {
   R q[5], g[kG], gr0[3], r0, E0;
 };
 
+// ------------------------------------------------------------------ wall flux
+
+// Conductive energy flux f.n through the outer wall with the temperature imposed there (Section 5):
+// T = T_top in f = -kappa rho T grad S - kappa_r rho C_p grad T written in rho and p.
+template <class R>
+__device__ __forceinline__ R wall_conduction(const R g[kG], const R nh[3], R krf, const PhysArg<R>& ph) {
+  const R RT = ph.Rgas * ph.T_top;
+  R fn = R(0);
+#pragma unroll
+  for (int b = 0; b < 3; ++b)
+    fn += -ph.CpR * (ph.kappa * (qdiv(g[9 + b], ph.gamma) - RT * g[b]) + krf * (g[9 + b] - RT * g[b])) * nh[b];
+  return fn;
+}
+
+// Common flux F_n through a wall face point (Section 5): exact inviscid flux (0, p n, 0); viscous
+// momentum flux = the normal traction only; energy: f.n from the gradient with T = T_top (outer wall,
+// kind -2) or the prescribed flux (inner wall; in the perturbation form the background residual
+// carries it).  g: the gradient record at the point; nh: the unit outward normal.
+template <bool PERT, class R>
+__device__ __forceinline__ void wall_flux(const Pt<R>& st, const R g[kG], const R nh[3], int kind, R krf,
+                                          const PhysArg<R>& ph, R Fh[5]) {
+  const R mu = st.rho * ph.nu;
+  R trac = R(0);
+#pragma unroll
+  for (int a = 0; a < 3; ++a)
+#pragma unroll
+    for (int b = 0; b < 3; ++b) trac += nh[a] * mu * sig(g, a, b) * nh[b];
+  Fh[0] = R(0);
+#pragma unroll
+  for (int a = 0; a < 3; ++a) Fh[1 + a] = (st.p - trac) * nh[a];
+  if (kind == -2) {
+    Fh[4] = wall_conduction(g, nh, krf, ph);
+  } else {
+    Fh[4] = PERT ? R(0) : -ph.bottom_flux;
+  }
+}
+
 // ------------------------------------------------------------------ gradient kernel
 
 // Lifted gradients, then the one-sided normal viscous flux F_v . n_out on every face point,
 // written for the neighbours: Tv[e][F][0..2] = tau n, Tv[e][F][3] = u.tau n - f.n.
+// On a wall side (face-kernel mode) the energy entry holds instead the wall's conductive flux f.n
+// with the top temperature imposed (used by k_face on the outer wall; Section 5).
 template <int N, bool PERT, class R, int EPB, int D, bool KR>
 __device__ __forceinline__ void face_visc_dir(const KArgs<R>& A, const R* sm, int el, int ln, int e,
                                               const R (&s3f)[2][3]) {
@@ -713,14 +816,15 @@ __device__ __forceinline__ void face_visc_dir(const KArgs<R>& A, const R* sm, in
   for (int v = 0; v < 5; ++v) load_line_lin<N, D>(sq + v * N3, ln, qv[v]);
   load_grad_lines<N, D>(sg, ln, gv);
   if (PERT) {
-    load_line_lin<N, D>(sbg, ln, r0);
-    load_line_lin<N, D>(sbg + N3, ln, E0l);
+    load_line_bg<N, D>(sbg, ln, r0);
+    load_line_bg<N, D>(sbg + N3, ln, E0l);
 #pragma unroll
-    for (int n = 0; n < 3; ++n) load_line_lin<N, D>(sgr0 + n * N3, ln, g0[n]);
+    for (int n = 0; n < 3; ++n) load_line_bg<N, D>(sgr0 + n * N3, ln, g0[n]);
   }
 #pragma unroll 1
   for (int side = 0; side < 2; ++side) {
     const int f = side ? N : 0;
+    const int kind = kFaceKernel ? __ldg(A.m.nbr + e * 6 + 2 * D + side) : 0;
     R w[N];
 #pragma unroll
     for (int s = 0; s < N; ++s) w[s] = tI[f * N + s];
@@ -755,8 +859,10 @@ __device__ __forceinline__ void face_visc_dir(const KArgs<R>& A, const R* sm, in
     const R im = qdiv(sgn, mag);
     const R nh[3] = {im * s3[0], im * s3[1], im * s3[2]};
     const Pt<R> st = point_state<PERT>(qf, rho0f, E0f, A.ph);
+    const R krf = kr_at<N, D, KR>(A, e, ln, f);
     R Fv[5];
-    flux_visc<PERT>(st, gf, gr0f, rho0f, A.ph.gm1 * E0f, nh, A.ph, kr_at<N, D, KR>(A, e, ln, f), Fv);
+    flux_visc<PERT>(st, gf, gr0f, rho0f, A.ph.gm1 * E0f, nh, A.ph, krf, Fv);
+    if (kFaceKernel && kind < 0) Fv[4] = wall_conduction(gf, nh, krf, A.ph);
     R* o = A.Tv_out + ((size_t)e * 6 + 2 * D + side) * 4 * N2;
 #pragma unroll
     for (int v = 0; v < 4; ++v) o[v * N2 + ln] = Fv[1 + v];
@@ -780,7 +886,7 @@ __global__ void __launch_bounds__(EPB * N * N, sizeof(R) == 4 ? grad_min_blocks<
   __syncthreads();
   LiftPre<N, R> pre;
   if (!stage_elements<N, PERT, R, EPB, false>(A, sm, &bar, ne, [&] {
-        if (active) lift_prefetch<N, PERT, R, kLiftFused ? 1 : 0>(A, e, ln, pre);
+        if (active) lift_prefetch<N, PERT, R, kLiftFused ? lift_dir_at<N, R>(0) : 0>(A, e, ln, pre);
       }))
     return;
   lift_all<N, PERT, R, EPB>(A, sm, el, ln, e, active, pre);
@@ -874,8 +980,20 @@ __device__ __forceinline__ void flux_dir(const KArgs<R>& A, R* sm, int el, int l
   }
   NbFace<R> nbn;  // mode 2: the next end point's neighbour data
   nbn.kind = -1;
+  // face-kernel mode: the end points' common fluxes F~ are read (both issued now), and the loop visits
+  // the interior flux points 1..N-1 only
+  constexpr bool FK = kFaceKernel;
+  R Fc0[FK ? 5 : 1], FcN[FK ? 5 : 1];
+  if constexpr (FK) {
+    const R* c0 = A.Fc + ((size_t)e * 6 + 2 * D) * 5 * N2 + ln;
+#pragma unroll
+    for (int v = 0; v < 5; ++v) {
+      Fc0[v] = __ldg(c0 + v * N2);
+      FcN[v] = __ldg(c0 + (5 + v) * N2);
+    }
+  }
 #pragma unroll 1
-  for (int it = 0; it <= N; ++it) {
+  for (int it = 0; it < (FK ? N - 1 : N + 1); ++it) {
     const int f = flux_order<N, EF>(it);
     R s3[3];
     if constexpr (SMM) {
@@ -900,7 +1018,7 @@ __device__ __forceinline__ void flux_dir(const KArgs<R>& A, R* sm, int el, int l
       for (int n = 0; n < 3; ++n) s3n[n] = __ldg(Sl + (n * (N + 1) + fn) * N2 + ln);
     }
     NbFace<R> nbc;  // mode 2: this end point's neighbour data
-    if (flux_nb_mode<N>() == 2) {
+    if (!FK && flux_nb_mode<N>() == 2) {
       nbc = nbn;
       if (it == N - 2 || it == N - 1) nbn = load_nb_at<N, PERT, true>(A, pre.nbi[it == N - 2 ? 1 : 0]);
     }
@@ -932,7 +1050,7 @@ __device__ __forceinline__ void flux_dir(const KArgs<R>& A, R* sm, int el, int l
     if (PERT) {
 #pragma unroll
       for (int s = 0; s < N; ++s) {
-        const int pt = line_pt<N, D>(ln, s);
+        const int pt = line_bg<N, D, R>(ln, s);
         if constexpr (L::bgShared) {
           P.r0 += w[s] * sbg[pt];
           P.E0 += w[s] * sbg[N3 + pt];
@@ -952,7 +1070,7 @@ __device__ __forceinline__ void flux_dir(const KArgs<R>& A, R* sm, int el, int l
     const R p0f = ph.gm1 * P.E0;
     const R krf = kr_at<N, D, KR>(A, e, ln, f);
     R Ft[5];
-    if (f > 0 && f < N) {
+    if (FK || (f > 0 && f < N)) {
       R Fi[5], Fv[5];
       flux_inv(P.q, st, s3, Fi);
       flux_visc<PERT>(st, P.g, P.gr0, P.r0, p0f, s3, ph, krf, Fv);
@@ -990,29 +1108,7 @@ __device__ __forceinline__ void flux_dir(const KArgs<R>& A, R* sm, int el, int l
         for (int v = 1; v < 5; ++v)  // the neighbour stored F_v . n_out(neighbour) = -F_v . n
           Fh[v] -= R(0.5) * (Fv[v] - nb.tv[v - 1]);
       } else {
-        // walls (Section 5): exact inviscid flux (0, p n, 0); normal traction only;
-        // energy: f.n from the lifted gradient with T = T_top (outer) or the prescribed flux (inner)
-        const R mu = st.rho * ph.nu;
-        R trac = R(0);
-#pragma unroll
-        for (int a = 0; a < 3; ++a)
-#pragma unroll
-          for (int b = 0; b < 3; ++b) trac += nh[a] * mu * sig(P.g, a, b) * nh[b];
-        Fh[0] = R(0);
-#pragma unroll
-        for (int a = 0; a < 3; ++a) Fh[1 + a] = (st.p - trac) * nh[a];
-        if (nb.kind == -2) {
-          const R RT = ph.Rgas * ph.T_top;
-          R fn = R(0);
-#pragma unroll
-          for (int b = 0; b < 3; ++b)
-            fn += -ph.CpR *
-                  (ph.kappa * (qdiv(P.g[9 + b], ph.gamma) - RT * P.g[b]) + krf * (P.g[9 + b] - RT * P.g[b])) *
-                  nh[b];
-          Fh[4] = fn;
-        } else {
-          Fh[4] = PERT ? R(0) : -ph.bottom_flux;
-        }
+        wall_flux<PERT>(st, P.g, nh, nb.kind, krf, ph, Fh);  // walls (Section 5)
       }
 #pragma unroll
       for (int v = 0; v < 5; ++v) Ft[v] = sgn * mag * Fh[v];
@@ -1022,6 +1118,14 @@ __device__ __forceinline__ void flux_dir(const KArgs<R>& A, R* sm, int el, int l
       const R dc = tD[i * (N + 1) + f];
 #pragma unroll
       for (int v = 0; v < 5; ++v) acc[v][i] += dc * Ft[v];
+    }
+  }
+  if constexpr (FK) {
+#pragma unroll
+    for (int i = 0; i < N; ++i) {
+      const R d0 = tD[i * (N + 1)], dN = tD[i * (N + 1) + N];
+#pragma unroll
+      for (int v = 0; v < 5; ++v) acc[v][i] += d0 * Fc0[v] + dN * FcN[v];
     }
   }
 #pragma unroll
@@ -1079,7 +1183,7 @@ __global__ void __launch_bounds__(EPB * N * N, sizeof(R) == 4 ? resid_min_blocks
   __shared__ int snb[flux_nb_mode<N>() == 3 ? EPB : 1][12];  // (neighbour, face code) of the 6 faces
   if (!stage_elements<N, PERT, R, EPB, true>(A, sm, &bar, ne, [&] {
         if (active) flux_prefetch<N, PERT, R, 0>(A, e, ln, fp);
-        if (flux_nb_mode<N>() == 3 && active && ln < 6) {
+        if (!kFaceKernel && flux_nb_mode<N>() == 3 && active && ln < 6) {
           snb[el][2 * ln] = __ldg(A.m.nbr + e * 6 + ln);
           snb[el][2 * ln + 1] = __ldg(A.m.code + e * 6 + ln);
         }
@@ -1189,6 +1293,101 @@ __global__ void __launch_bounds__(EPB * N * N, sizeof(R) == 4 ? resid_min_blocks
   }
 }
 
+// ------------------------------------------------------------------ face kernel
+
+// Common flux of every interior face point, once per face (Section 3: Rusanov inviscid flux with the
+// wave speed of both sides, average of the two one-sided normal viscous fluxes from the lifting
+// kernel).  One thread per (face, point) of the face list (element, local face) of owner sides; the
+// owner's metric gives the unit normal n and |S|.  Writes F~ = sigma |S| F_n at the owner's point and
+// -sigma' |S| F_n at the neighbour's matching point (its outward normal is -n), so the two sides'
+// fluxes are exactly opposite.
+//
+// Wall faces follow the interior ones in the list (entries nf..nf+nw-1): their common flux (Section 5)
+// is formed from the element's own trace and the lifting kernel's wall data (the viscous traction
+// tau n and the conductive flux with the top temperature imposed).
+template <int N, bool PERT, class R>
+__global__ void __launch_bounds__(128) k_face(const KArgs<R> A, const int2* __restrict__ faces, int nf, int nw) {
+  constexpr int N2 = N * N;
+  const int64_t g = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (g >= (int64_t)(nf + nw) * N2) return;
+  const int t = (int)(g % N2);
+  const int2 fc = faces[g / N2];
+  const int e = fc.x, F = fc.y, D = F >> 1, side = F & 1;
+  const int k = __ldg(A.m.nbr + e * 6 + F), code = __ldg(A.m.code + e * 6 + F);
+  if (k < 0) {  // wall
+    const size_t o = (size_t)e * 6 + F;
+    R q[5], tv[4];
+#pragma unroll
+    for (int v = 0; v < 5; ++v) q[v] = __ldg(A.T + (o * 5 + v) * N2 + t);
+#pragma unroll
+    for (int v = 0; v < 4; ++v) tv[v] = __ldg(A.Tv + (o * 4 + v) * N2 + t);
+    R r0 = R(0), E0 = R(0);
+    if (PERT) {
+      r0 = (R)__ldg(A.bg.bgT + (o * 2) * N2 + t);
+      E0 = (R)__ldg(A.bg.bgT + (o * 2 + 1) * N2 + t);
+    }
+    const R* Sl = A.m.Sf + ((size_t)e * 3 + D) * 3 * (N + 1) * N2;
+    R s3[3];
+#pragma unroll
+    for (int n = 0; n < 3; ++n) s3[n] = __ldg(Sl + (n * (N + 1) + (side ? N : 0)) * N2 + t);
+    const R sgn = side ? R(1) : R(-1);
+    const R mag = sqrt(s3[0] * s3[0] + s3[1] * s3[1] + s3[2] * s3[2]);
+    const R im = qdiv(sgn, mag);
+    const R nh[3] = {im * s3[0], im * s3[1], im * s3[2]};
+    const Pt<R> st = point_state<PERT>(q, r0, E0, A.ph);
+    // exact inviscid flux (0, p n, 0) minus the normal viscous traction; energy: f.n
+    const R trac = tv[0] * nh[0] + tv[1] * nh[1] + tv[2] * nh[2];
+    R Fh[5];
+    Fh[0] = R(0);
+#pragma unroll
+    for (int a = 0; a < 3; ++a) Fh[1 + a] = (st.p - trac) * nh[a];
+    Fh[4] = k == -2 ? tv[3] : (PERT ? R(0) : -A.ph.bottom_flux);
+#pragma unroll
+    for (int v = 0; v < 5; ++v) A.Fc_out[(o * 5 + v) * N2 + t] = sgn * mag * Fh[v];
+    return;
+  }
+  const int Fn = code >> 3, tp = map_face_pt<N>(t, code & 7);
+  const size_t oL = (size_t)e * 6 + F, oR = (size_t)k * 6 + Fn;
+  R qL[5], qR[5], tvL[4], tvR[4];
+#pragma unroll
+  for (int v = 0; v < 5; ++v) {
+    qL[v] = __ldg(A.T + (oL * 5 + v) * N2 + t);
+    qR[v] = __ldg(A.T + (oR * 5 + v) * N2 + tp);
+  }
+#pragma unroll
+  for (int v = 0; v < 4; ++v) {
+    tvL[v] = __ldg(A.Tv + (oL * 4 + v) * N2 + t);
+    tvR[v] = __ldg(A.Tv + (oR * 4 + v) * N2 + tp);
+  }
+  R r0L = R(0), E0L = R(0), r0R = R(0), E0R = R(0);
+  if (PERT) {
+    r0L = (R)__ldg(A.bg.bgT + (oL * 2) * N2 + t);
+    E0L = (R)__ldg(A.bg.bgT + (oL * 2 + 1) * N2 + t);
+    r0R = (R)__ldg(A.bg.bgT + (oR * 2) * N2 + tp);
+    E0R = (R)__ldg(A.bg.bgT + (oR * 2 + 1) * N2 + tp);
+  }
+  const R* Sl = A.m.Sf + ((size_t)e * 3 + D) * 3 * (N + 1) * N2;
+  R s3[3];
+#pragma unroll
+  for (int n = 0; n < 3; ++n) s3[n] = __ldg(Sl + (n * (N + 1) + (side ? N : 0)) * N2 + t);
+  const R sgn = side ? R(1) : R(-1);
+  const R mag = sqrt(s3[0] * s3[0] + s3[1] * s3[1] + s3[2] * s3[2]);
+  const R im = qdiv(sgn, mag);
+  const R nh[3] = {im * s3[0], im * s3[1], im * s3[2]};
+  const Pt<R> sL = point_state<PERT>(qL, r0L, E0L, A.ph);
+  const Pt<R> sR = point_state<PERT>(qR, r0R, E0R, A.ph);
+  R Fh[5];
+  rusanov<PERT>(qL, sL, r0L, E0L, qR, sR, r0R, E0R, nh, A.ph, Fh);
+#pragma unroll
+  for (int v = 1; v < 5; ++v) Fh[v] -= R(0.5) * (tvL[v - 1] - tvR[v - 1]);  // tvR = F_v,R . (-n)
+  const R sR_ = (Fn & 1) ? R(1) : R(-1);
+#pragma unroll
+  for (int v = 0; v < 5; ++v) {
+    A.Fc_out[(oL * 5 + v) * N2 + t] = sgn * mag * Fh[v];
+    A.Fc_out[(oR * 5 + v) * N2 + tp] = -sR_ * mag * Fh[v];
+  }
+}
+
 // ------------------------------------------------------------------ launch helpers
 
 template <int N, bool PERT, class R, int EPB>
@@ -1200,6 +1399,13 @@ struct Launch {
   static cudaError_t trace(const MeshArg<R>& m, const OpsArg<R>& ops, const R* q, R* T, cudaStream_t st) {
     if (m.E == 0) return cudaSuccess;
     k_trace<N, R, EPB><<<blocks(m.E), threads, 0, st>>>(m, ops, q, T);
+    return cudaGetLastError();
+  }
+  static cudaError_t face(const KArgs<R>& A, const int2* faces, int nf, int nw, cudaStream_t st) {
+    if (!kFaceKernel || nf + nw == 0) return cudaSuccess;
+    if (A.Fc_out == nullptr || A.T == nullptr || A.Tv == nullptr) return cudaErrorInvalidValue;
+    const int64_t n = (int64_t)(nf + nw) * N * N;
+    k_face<N, PERT, R><<<(unsigned)((n + 127) / 128), 128, 0, st>>>(A, faces, nf, nw);
     return cudaGetLastError();
   }
   static cudaError_t grad(const KArgs<R>& A, cudaStream_t st) {
@@ -1224,6 +1430,7 @@ struct Launch {
   static cudaError_t resid(const KArgs<R>& A, cudaStream_t st) {
     if (A.m.E == 0) return cudaSuccess;
     if (A.G_in == nullptr) return cudaErrorInvalidValue;  // the residual kernel reads the gradient record
+    if (kFaceKernel && A.Fc == nullptr) return cudaErrorInvalidValue;  // and the common face fluxes
     const size_t sm = (size_t)Layout<N, PERT, R, EPB, true>::total_resid * sizeof(R);
     if constexpr (sizeof(R) == 8) {
       return resid_kr<MODE, true>(A, st, sm);

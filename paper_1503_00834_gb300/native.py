@@ -250,9 +250,10 @@ class Mesh:
         _ok("chorus_timing_enable", load().chorus_timing_enable(self.handle, 1 if enable else 0))
 
     def timing_read(self, stream=None):
-        """(ms[3], counts[3]) per kernel class: 0 traces, 1 gradients, 2 residual/RK update."""
-        ms = (ctypes.c_double * 3)()
-        cnt = (ctypes.c_int64 * 3)()
+        """(ms[4], counts[4]) per kernel class: 0 traces, 1 gradients (and wall fluxes), 2 residual/RK
+        update, 3 interior-face common fluxes."""
+        ms = (ctypes.c_double * 4)()
+        cnt = (ctypes.c_int64 * 4)()
         _ok("chorus_timing_read", load().chorus_timing_read(self.handle, _stream(stream), ms, cnt))
         return list(ms), list(cnt)
 

@@ -2,8 +2,8 @@
 
 Such callers (for example an application whose device memory belongs to its own pool allocator,
 or a loop that must not call cudaMalloc because it can synchronise the device) pass only Q and R;
-the library keeps its scratch (traces, viscous face fluxes, gradient record) in a fixed static device
-array.  This test calls the
+the library keeps its scratch (traces, viscous face fluxes, gradient record, common face fluxes) in a
+fixed static device array.  This test calls the
 entry point through the C ABI twice in a row, on two different states, and checks each result
 against chorus_residual with a caller-provided workspace, within the parity tolerances the other
 GPU tests use (1e-12 relative for FP64, 1e-5 for the FP32 perturbation path).  It also checks that a
@@ -68,7 +68,7 @@ def test_noalloc_refuses_meshes_beyond_the_scratch():
     from paper_1503_00834_gb300 import FP32_PERT, FP64, Shell, load
 
     lib = load()
-    cfg = small_shell(12, 5, 3)  # 4,320 elements: 56.4 MB of FP64 scratch, 28.2 MB in FP32 (limit 32 MiB)
+    cfg = small_shell(10, 5, 3)  # 3,000 elements: 50.7 MB of FP64 scratch, 25.3 MB in FP32 (limit 32 MiB)
     sh = Shell(cfg)
     Q = torch.zeros(sh.mesh.state_shape(), dtype=torch.float64, device="cuda")
     R = torch.zeros_like(Q)
