@@ -313,8 +313,9 @@ chorus_status chorus_residual_noalloc(chorus_mesh mesh, const chorus_params* par
  * of the same discretisation, Sections 3-5).  All shells share the radii and the physical
  * parameters; each has its own mesh, order and seeded perturbation.
  *  - Shells of one order form one internal mesh (their disjoint union), so each kernel of an RK
- *    stage is one launch per order present, and the orders run concurrently on forked streams.
- *    One RK step of the whole batch is captured once as a CUDA graph and replayed.
+ *    stage is one launch per order present; the orders run concurrently on forked streams or one
+ *    after another (chorus_batch_schedule; the autotuner picks the faster).  One RK step of the
+ *    whole batch is captured once as a CUDA graph and replayed.
  *  - State: FP32 perturbation form (CHORUS_FP32_PERT) only.  One caller-owned device array holds
  *    every shell; shell s occupies [state_offset[s], state_offset[s] + n_elem_s * 5 * N_s^3)
  *    floats, in the single-mesh layout of its own order.
@@ -359,13 +360,18 @@ chorus_status chorus_batch_rk_step(chorus_batch batch, float* Q, void* workspace
  * (mass, total energy, kinetic energy, |L|).  Synchronises. */
 chorus_status chorus_batch_reduce(chorus_batch batch, const float* Q, double* out, void* stream);
 
-/* Tile-shape autotuner: for each order, times n_trials RK steps with every built tile shape
- * (elements per CTA) of the FP32 kernels on this batch's own meshes, keeps the fastest and drops
- * the captured graph.  Q and workspace are scratch (their contents are overwritten).  choice: host
- * int[4] receiving the chosen elements per CTA for p = 2..5 (0 where the order is absent), or NULL.
- * Synchronises. */
+/* Autotuner: for each order, times n_trials RK steps with every built tile shape (elements per CTA)
+ * of the FP32 kernels on this batch's own meshes and keeps the fastest; then times n_trials replays
+ * of the captured step with the orders on concurrent streams and with the orders one after another,
+ * keeps the faster schedule, and drops the captured graph.  Q and workspace are scratch (their
+ * contents are overwritten).  choice: host int[4] receiving the chosen elements per CTA for
+ * p = 2..5 (0 where the order is absent), or NULL.  Synchronises. */
 chorus_status chorus_batch_autotune(chorus_batch batch, float* Q, void* workspace, double dt, int n_trials,
                                     void* stream, int* choice);
+
+/* Schedule of the orders within a batch step: set 1 = concurrent streams, 0 = one after another,
+ * any other value leaves it; concurrent: host int receiving the schedule in force, or NULL. */
+chorus_status chorus_batch_schedule(chorus_batch batch, int set, int* concurrent);
 
 /* Well-balanced perturbation residual (FP32_PERT only; a library option the paper has no
  * counterpart for).  The residual of Q0 + q' becomes R(Q0 + q') - R(Q0): the discrete residual of the

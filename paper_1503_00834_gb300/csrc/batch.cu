@@ -1,8 +1,9 @@
 // Batched independent shells (declared in include/chorus.h): the shells of one order form one
 // mesh (their disjoint union: the face pairing joins only faces that share nodes, and the shells
-// share none), the orders run concurrently on streams forked from the caller's stream, one RK step
-// of the whole batch is captured as a CUDA graph and replayed, and a small autotuner picks the FP32
-// tile shape per order on the batch's own meshes.
+// share none), the orders run either concurrently on streams forked from the caller's stream or one
+// after another on it, one RK step of the whole batch is captured as a CUDA graph and replayed, and a
+// small autotuner picks the FP32 tile shape per order on the batch's own meshes and then the faster
+// of the two schedules.
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -38,6 +39,7 @@ struct chorus_batch_s {
   size_t ws_bytes = 0;
   cudaEvent_t fork = nullptr;
   cudaStream_t cap = nullptr;  // capture stream (the caller's may be the legacy stream, which cannot be captured)
+  bool concurrent = true;  // orders on forked streams (true) or one after another (false)
   cudaGraphExec_t exec = nullptr;
   const float* g_Q = nullptr;
   const void* g_ws = nullptr;
@@ -68,8 +70,16 @@ void free_batch(chorus_batch_s* b) {
   delete b;
 }
 
-// One RK step of every group, forked from and joined back into `st`.
+// One RK step of every group: forked from and joined back into `st`, or one group after another on it.
 chorus_status step_all(chorus_batch_s* b, float* Q, void* ws, double dt, cudaStream_t st) {
+  if (!b->concurrent) {
+    for (auto& g : b->groups) {
+      const chorus_status s = chorus_rk_step_scheme(g.mesh, &b->params, CHORUS_FP32_PERT, 0, Q + g.state_off,
+                                                    (char*)ws + g.ws_off, dt, 1, st);
+      if (s != CHORUS_OK) return s;
+    }
+    return CHORUS_OK;
+  }
   if (cudaEventRecord(b->fork, st) != cudaSuccess) return CHORUS_ECUDA;
   for (auto& g : b->groups) {
     if (cudaStreamWaitEvent(g.stream, b->fork, 0) != cudaSuccess) return CHORUS_ECUDA;
@@ -241,7 +251,7 @@ chorus_status chorus_batch_init(chorus_batch b, float* Q, void* stream) {
 chorus_status chorus_batch_rk_step(chorus_batch b, float* Q, void* workspace, double dt, int64_t n_steps,
                                    void* stream, int64_t* launches) {
   if (!b || !Q || !workspace || !(dt > 0.0) || !std::isfinite(dt) || n_steps < 0) return CHORUS_EINVAL;
-  if (launches) *launches = 7 * (int64_t)b->groups.size();  // per order: trace + 3 x (gradient, residual)
+  if (launches) *launches = 10 * (int64_t)b->groups.size();  // per order: trace + 3 x (gradient, face, residual)
   if (n_steps == 0) return CHORUS_OK;
   cudaStream_t st = (cudaStream_t)stream;
   if (!b->exec || b->g_Q != Q || b->g_ws != workspace || b->g_dt != dt) {
@@ -314,9 +324,34 @@ chorus_status chorus_batch_autotune(chorus_batch b, float* Q, void* workspace, d
     const int epb = mesh_set_tile(g.mesh, best);
     if (choice) choice[g.p - 2] = epb;
   }
+  // then the schedule: the captured step with the orders concurrent and one after another
+  float sched_ms[2] = {0.0f, 0.0f};
+  for (int c = 0; c < 2 && status == CHORUS_OK; ++c) {
+    b->concurrent = c == 0;
+    status = capture(b, Q, workspace, dt);
+    if (status == CHORUS_OK && cudaGraphLaunch(b->exec, st) != cudaSuccess) status = CHORUS_ECUDA;  // warm-up
+    if (status == CHORUS_OK && cudaEventRecord(t0, st) != cudaSuccess) status = CHORUS_ECUDA;
+    for (int n = 0; n < n_trials && status == CHORUS_OK; ++n)
+      if (cudaGraphLaunch(b->exec, st) != cudaSuccess) status = CHORUS_ECUDA;
+    if (status == CHORUS_OK && (cudaEventRecord(t1, st) != cudaSuccess || cudaEventSynchronize(t1) != cudaSuccess ||
+                                cudaEventElapsedTime(&sched_ms[c], t0, t1) != cudaSuccess))
+      status = CHORUS_ECUDA;
+  }
+  b->concurrent = sched_ms[0] <= sched_ms[1];
+  drop_graph(b);
   cudaEventDestroy(t0);
   cudaEventDestroy(t1);
   return status;
+}
+
+chorus_status chorus_batch_schedule(chorus_batch b, int set, int* concurrent) {
+  if (!b) return CHORUS_EINVAL;
+  if (set == 0 || set == 1) {
+    if (b->concurrent != (set == 1)) drop_graph(b);
+    b->concurrent = set == 1;
+  }
+  if (concurrent) *concurrent = b->concurrent ? 1 : 0;
+  return CHORUS_OK;
 }
 
 }  // extern "C"

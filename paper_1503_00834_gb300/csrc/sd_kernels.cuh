@@ -153,7 +153,10 @@ struct Layout {
   static constexpr int SDIV = pad_stride<R>(5 * N3);
   // staged metric blocks of one direction (residual kernel, when stage_metrics)
   static constexpr bool SM = RES && stage_metrics<N, R>();
-  static constexpr int SSF = SM ? 3 * (N + 1) * N2 : 0;
+  // face-kernel mode visits the interior flux points 1..N-1 only: their metrics are all it stages
+  static constexpr int SFP = kFaceKernel ? N - 1 : N + 1;  // staged flux points per line
+  static constexpr int SF0 = kFaceKernel ? 1 : 0;          // first staged flux point
+  static constexpr int SSF = SM ? 3 * SFP * N2 : 0;
   // interpolation I[f][s] and derivative D[i][f] tables, indexed at run time by rolled loops
   static constexpr int TAB = pad_stride<R>(2 * (N + 1) * N);
   static constexpr int oTAB = 0;
@@ -460,6 +463,17 @@ __global__ void __launch_bounds__(EPB * N * N) k_trace(const MeshArg<R> m, const
 
 // ------------------------------------------------------------------ staging
 
+// Bulk copies of element e's direction-d metrics S^d_n at the staged flux points (L::SF0 ..
+// L::SF0 + L::SFP - 1), one copy per component n, into `dst` as [n][staged point][line].
+template <int N, class R, class L>
+__device__ __forceinline__ void stage_metric_block(const R* Sf, int64_t e, int d, R* dst, uint64_t* bar) {
+  constexpr int N2 = N * N;
+#pragma unroll
+  for (int n = 0; n < 3; ++n)
+    bulk_g2s(dst + n * L::SFP * N2, Sf + (((size_t)e * 3 + d) * 3 + n) * (N + 1) * N2 + L::SF0 * N2,
+             L::SFP * N2 * sizeof(R), bar);
+}
+
 // `between` runs after the copies are issued and before the wait (it issues the first sweep's
 // global loads so that both latencies overlap).  Returns false, the same in every thread of the CTA,
 // when the bounded wait for the copies ran out (the flag is set in *A.err and the copies in flight
@@ -485,8 +499,7 @@ __device__ __forceinline__ bool stage_elements(const KArgs<R>& A, R* sm, uint64_
     if (L::SM) bytes += ne * L::SSF * sizeof(R);
     mbar_expect_tx(bar, bytes);
     if constexpr (L::SM) {
-      for (int el = 0; el < ne; ++el)
-        bulk_g2s(sm + L::oSF0 + el * L::SSF, A.m.Sf + ((size_t)(e0 + el) * 3) * L::SSF, L::SSF * sizeof(R), bar);
+      for (int el = 0; el < ne; ++el) stage_metric_block<N, R, L>(A.m.Sf, e0 + el, 0, sm + L::oSF0 + el * L::SSF, bar);
     }
     for (int el = 0; el < ne; ++el) {
       if (tg) bulk_g2s(sm + L::oG + el * L::SG, A.G_in + (size_t)(e0 + el) * kG * N3, kG * N3 * sizeof(R), bar);
@@ -998,7 +1011,7 @@ __device__ __forceinline__ void flux_dir(const KArgs<R>& A, R* sm, int el, int l
     R s3[3];
     if constexpr (SMM) {
 #pragma unroll
-      for (int n = 0; n < 3; ++n) s3[n] = sS[(n * (N + 1) + f) * N2 + ln];
+      for (int n = 0; n < 3; ++n) s3[n] = sS[(n * L::SFP + f - L::SF0) * N2 + ln];
     } else {
 #pragma unroll
       for (int n = 0; n < 3; ++n) s3[n] = s3n[n];
@@ -1171,8 +1184,7 @@ __global__ void __launch_bounds__(EPB * N * N, sizeof(R) == 4 ? resid_min_blocks
         fence_async_smem();  // the buffer's previous contents were read by the generic proxy
         mbar_expect_tx(b, ne * L::SSF * sizeof(R));
         for (int j = 0; j < ne; ++j)
-          bulk_g2s(sm + (buf ? L::oSF1 : L::oSF0) + j * L::SSF, A.m.Sf + ((size_t)(e0 + j) * 3 + d) * L::SSF,
-                   L::SSF * sizeof(R), b);
+          stage_metric_block<N, R, L>(A.m.Sf, e0 + j, d, sm + (buf ? L::oSF1 : L::oSF0) + j * L::SSF, b);
       }
     }
   };

@@ -31,7 +31,7 @@ EXPORTS = ("chorus_mesh_create", "chorus_mesh_destroy", "chorus_mesh_info", "cho
            "chorus_batch_destroy", "chorus_batch_layout", "chorus_batch_init", "chorus_batch_rk_step",
            "chorus_batch_reduce", "chorus_batch_autotune", "chorus_set_well_balanced", "chorus_prepare_profile",
            "chorus_afb_profile", "chorus_closure_set_scales", "chorus_stable_dt_rule", "chorus_stable_dt",
-           "chorus_set_wait_limit", "chorus_fma_rate", "chorus_rk_step_host")
+           "chorus_set_wait_limit", "chorus_fma_rate", "chorus_rk_step_host", "chorus_batch_schedule")
 
 
 class ChorusError(RuntimeError):
@@ -123,6 +123,7 @@ def load() -> ctypes.CDLL:
         "chorus_set_wait_limit": (i32, [vp, i64]),
         "chorus_fma_rate": (i32, [i32, vp, P(f64)]),
         "chorus_rk_step_host": (i32, [vp, P(Params), i32, vp, vp, vp, f64, i64, vp]),
+        "chorus_batch_schedule": (i32, [vp, i32, P(i32)]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(lib, name)
@@ -347,6 +348,13 @@ class Batch:
         out = (ctypes.c_double * (4 * len(self.orders)))()
         _ok("chorus_batch_reduce", load().chorus_batch_reduce(self.handle, _ptr(Q), out, _stream(stream)))
         return np.array(out[:]).reshape(-1, 4)
+
+    def schedule(self, concurrent=None) -> bool:
+        """The schedule of the orders in a step (True: concurrent streams); sets it when given."""
+        out = ctypes.c_int()
+        set_ = -1 if concurrent is None else (1 if concurrent else 0)
+        _ok("chorus_batch_schedule", load().chorus_batch_schedule(self.handle, set_, ctypes.byref(out)))
+        return bool(out.value)
 
     def autotune(self, Q, ws, dt: float, n_trials: int = 3, stream=None):
         """Chosen elements per CTA for p = 2..5 (0 where absent)."""
