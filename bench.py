@@ -424,6 +424,8 @@ def main():
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--workload", default=None, choices=["batch_64"])
+    ap.add_argument("--closure", action="store_true",
+                    help="attach a seeded learned-closure record (p = 2 shells): every stage adds the network")
     args = ap.parse_args()
     cfg = CONFIGS[args.config]
     rank, world, local = _dist()
@@ -473,6 +475,12 @@ def main():
     mesh.prepare(sh.params)
     mesh.state_init(sh.params, cfg.seed, cfg.entropy_amp, prec, Q)
     n_dof = cfg.n_dof
+    closure_rec = None
+    if args.closure:
+        if cfg.p != 2:
+            raise SystemExit("--closure needs a p = 2 shell (the closure's order)")
+        closure_rec = native.closure_alloc(11, [1e-4] * 5, [1e-5] * 5)
+        native.closure_attach(mesh, closure_rec)
     # measured arithmetic peaks of this GPU (the FP64 path is bound by its FP64 units)
     fma = {"fp64_tflops": native.fma_rate(FP64) / 1e12, "fp32_tflops": native.fma_rate(FP32_PERT) / 1e12}
 
@@ -562,7 +570,8 @@ def main():
             "data": "synthetic",
             "config": {"workload": cfg.name, "elements": cfg.n_elem, "p": cfg.p, "dof": n_dof,
                        "precision": "FP32 perturbation + FP64 background" if prec == FP32_PERT else "FP64",
-                       "step": "one SSP-RK3 step = 3 residual + stage-update passes",
+                       "step": "one SSP-RK3 step = 3 residual + stage-update passes"
+                               + (" with the learned closure attached" if args.closure else ""),
                        "l2": "inputs larger than L2 (state %.0f MB)" % (state_bytes / 1e6),
                        "parallelism": f"replicas x{world}"},
             "roofline": roof,

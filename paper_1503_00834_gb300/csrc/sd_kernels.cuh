@@ -153,9 +153,11 @@ struct Layout {
   static constexpr int SDIV = pad_stride<R>(5 * N3);
   // staged metric blocks of one direction (residual kernel, when stage_metrics)
   static constexpr bool SM = RES && stage_metrics<N, R>();
-  // face-kernel mode visits the interior flux points 1..N-1 only: their metrics are all it stages
-  static constexpr int SFP = kFaceKernel ? N - 1 : N + 1;  // staged flux points per line
-  static constexpr int SF0 = kFaceKernel ? 1 : 0;          // first staged flux point
+  // staged flux points per line and the first of them: all N + 1 (one 960-byte copy per element and
+  // direction at N = 4); staging only the interior points 1..N-1 that the face-kernel mode visits
+  // took three copies per element and direction and made the residual kernel 8 % slower
+  static constexpr int SFP = N + 1;
+  static constexpr int SF0 = 0;
   static constexpr int SSF = SM ? 3 * SFP * N2 : 0;
   // interpolation I[f][s] and derivative D[i][f] tables, indexed at run time by rolled loops
   static constexpr int TAB = pad_stride<R>(2 * (N + 1) * N);
@@ -463,15 +465,20 @@ __global__ void __launch_bounds__(EPB * N * N) k_trace(const MeshArg<R> m, const
 
 // ------------------------------------------------------------------ staging
 
-// Bulk copies of element e's direction-d metrics S^d_n at the staged flux points (L::SF0 ..
-// L::SF0 + L::SFP - 1), one copy per component n, into `dst` as [n][staged point][line].
+// Bulk copy of element e's direction-d metrics S^d_n at the staged flux points (L::SF0 ..
+// L::SF0 + L::SFP - 1) into `dst` as [n][staged point][line]: one copy when all points are staged,
+// else one per component n.
 template <int N, class R, class L>
 __device__ __forceinline__ void stage_metric_block(const R* Sf, int64_t e, int d, R* dst, uint64_t* bar) {
   constexpr int N2 = N * N;
+  const R* src = Sf + ((size_t)e * 3 + d) * 3 * (N + 1) * N2;
+  if constexpr (L::SFP == N + 1) {
+    bulk_g2s(dst, src, 3 * (N + 1) * N2 * sizeof(R), bar);
+  } else {
 #pragma unroll
-  for (int n = 0; n < 3; ++n)
-    bulk_g2s(dst + n * L::SFP * N2, Sf + (((size_t)e * 3 + d) * 3 + n) * (N + 1) * N2 + L::SF0 * N2,
-             L::SFP * N2 * sizeof(R), bar);
+    for (int n = 0; n < 3; ++n)
+      bulk_g2s(dst + n * L::SFP * N2, src + (n * (N + 1) + L::SF0) * N2, L::SFP * N2 * sizeof(R), bar);
+  }
 }
 
 // `between` runs after the copies are issued and before the wait (it issues the first sweep's

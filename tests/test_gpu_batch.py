@@ -68,7 +68,7 @@ def test_init_and_steps_equal_single_meshes(batch):
     b.init(Q)
     n_steps = 3
     launches = b.rk_step(Q, ws, batch.dt, n_steps)
-    assert launches == 7 * 4
+    assert launches == 10 * 4  # per order: trace + 3 x (lifting, face, residual)
     b.rk_step(Q, ws, batch.dt, 0)
     torch.cuda.synchronize()
     red = b.reduce(Q)
@@ -141,3 +141,23 @@ def test_autotune_picks_a_built_tile_and_keeps_results(batch):
         scale = q.abs().max().item()
         print(f"shell {s}: max |batch - single| = {d:.3e} (scale {scale:.3e})")
         assert d <= 1e-6 * scale
+
+
+def test_both_schedules_give_the_same_shells(batch):
+    """The orders one after another or on concurrent streams: the same kernels on disjoint data, so
+    every shell's state is bit-identical after three steps."""
+    b = batch.batch
+    was = b.schedule()
+    try:
+        out = []
+        for concurrent in (True, False):
+            assert b.schedule(concurrent) == concurrent
+            Q, ws = _alloc(batch)
+            b.init(Q)
+            b.rk_step(Q, ws, batch.dt, 3)
+            torch.cuda.synchronize()
+            out.append(Q)
+        for s in range(len(batch.cfgs)):
+            assert torch.equal(b.view(out[0], s), b.view(out[1], s)), s
+    finally:
+        b.schedule(was)
