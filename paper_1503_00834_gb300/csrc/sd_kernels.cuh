@@ -66,7 +66,7 @@ __device__ __forceinline__ int line_sidx(int ln, int s) {
 
 // Residual-kernel options (FP32 perturbation form): whether the background line data are staged in
 // shared memory (else read through L1 per flux point), and the resident CTAs per SM asked of the
-// compiler (register cap).
+// compiler (register cap) at N = 5.
 constexpr bool kResidBgShared = true;
 constexpr int kResidMinBlocksF32 = 3;
 // Resident lifting CTAs asked for at N = 5 (five-element CTAs: three fit the shared memory; with
@@ -82,10 +82,21 @@ constexpr bool kVecGradLoad = true;
 // shared memory per flux point).  N = 6 runs two CTAs of four elements per SM (shared memory) and
 // does best with the registers that allows; N = 5 asks for three CTAs of each kernel, with the
 // gradient lines in shared memory.
+// At N = 3 and 4 the kernels ask for a number of warps per SM whatever their CTA size: 12 for the
+// residual kernel (168 registers a thread) and 16 for the lifting kernel (128); smaller CTAs at the
+// same warp count measured faster for the residual kernel (p = 3: four-element CTAs, six per SM,
+// 8 % faster than eight-element CTAs, three per SM; p = 2: seven-element CTAs 4.6 % faster than
+// fourteen-element ones), for the lifting kernel even at p = 3 and 1 % slower at p = 2.
 template <int N, int EPB>
-__host__ __device__ constexpr int resid_min_blocks() { return N <= 5 ? kResidMinBlocksF32 : 2; }
-template <int N>
-__host__ __device__ constexpr int grad_min_blocks() { return N <= 4 ? 4 : N == 5 ? kGradMinBlocksN5 : 2; }
+__host__ __device__ constexpr int warps_per_cta() { return (EPB * N * N + 31) / 32; }
+template <int N, int EPB>
+__host__ __device__ constexpr int resid_min_blocks() {
+  return N <= 4 ? 12 / warps_per_cta<N, EPB>() : N == 5 ? kResidMinBlocksF32 : 2;
+}
+template <int N, int EPB>
+__host__ __device__ constexpr int grad_min_blocks() {
+  return N <= 4 ? 16 / warps_per_cta<N, EPB>() : N == 5 ? kGradMinBlocksN5 : 2;
+}
 template <int N>
 __host__ __device__ constexpr bool reg_grad_lines() { return N <= 4; }
 
@@ -994,9 +1005,9 @@ __device__ __forceinline__ void face_visc_dir(const KArgs<R>& A, const R* sm, in
   }
 }
 
-// FP32: four resident CTAs per SM (register cap 128; the shared memory of the lifting fits four)
+// FP32: 16 resident warps per SM at N = 3, 4 (register cap 128), as grad_min_blocks gives
 template <int N, bool PERT, class R, int EPB, bool KR>
-__global__ void __launch_bounds__(EPB * N * N, sizeof(R) == 4 ? grad_min_blocks<N>() : 1) k_grad(const KArgs<R> A) {
+__global__ void __launch_bounds__(EPB * N * N, sizeof(R) == 4 ? grad_min_blocks<N, EPB>() : 1) k_grad(const KArgs<R> A) {
   constexpr int N2 = N * N;
   extern __shared__ __align__(128) unsigned char smem_raw[];
   __shared__ __align__(8) uint64_t bar;
@@ -1266,7 +1277,7 @@ __device__ __forceinline__ void flux_dir(const KArgs<R>& A, R* sm, int el, int l
 
 // ------------------------------------------------------------------ residual kernel
 
-// FP32: ask for three resident CTAs per SM (register cap ~168 per thread)
+// FP32: 12 resident warps per SM at N = 3, 4 (register cap ~168 per thread), as resid_min_blocks gives
 template <int N, bool PERT, class R, int EPB, int MODE, bool KR>
 __global__ void __launch_bounds__(EPB * N * N, sizeof(R) == 4 ? resid_min_blocks<N, EPB>() : 1) k_resid(const KArgs<R> A) {
   using L = Layout<N, PERT, R, EPB, true>;
