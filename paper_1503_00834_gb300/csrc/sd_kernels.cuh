@@ -127,8 +127,9 @@ constexpr bool kFaceKernel = true;
 
 // The lifting kernel's viscous face pass reads each line component from shared memory once and keeps
 // only its values at the two end points (2 x 22 live values) instead of holding the whole line data
-// (22 x N values) through both end points.  Timed per order: the lifting kernel 2.5 % faster at
-// N = 4, 12 % at N = 6 (its spills gone), even at N = 5, 1.2 % slower at N = 3.
+// (22 x N values) through both end points, and evaluates the two end points with the side loop
+// unrolled.  Timed per order: the lifting kernel 8 % faster at N = 4, 12 % at N = 6 (its spills
+// gone), 2 % at N = 5; at N = 3 2.5 % slower.
 template <int N>
 __host__ __device__ constexpr bool face_ends() { return N >= 4; }
 
@@ -916,8 +917,8 @@ __device__ __forceinline__ void face_visc_dir(const KArgs<R>& A, const R* sm, in
         line_ends<N>(l, w0, wN, gre[0][n], gre[1][n]);
       }
     }
-#pragma unroll 1
-    for (int side = 0; side < 2; ++side) {
+#pragma unroll
+    for (int side = 0; side < 2; ++side) {  // unrolled: the end values are picked by constant index
       const int f = side ? N : 0;
       const int kind = kFaceKernel ? __ldg(A.m.nbr + e * 6 + 2 * D + side) : 0;
       R qf[5], gf[kG], gr0f[3];
