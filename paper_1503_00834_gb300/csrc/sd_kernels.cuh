@@ -133,6 +133,10 @@ constexpr bool kFaceKernel = true;
 template <int N>
 __host__ __device__ constexpr bool face_ends() { return N >= 4; }
 
+// Whether the lifting kernel stages each element's six (neighbour, face code) pairs in shared memory
+// with its element blocks, so that the later directions' neighbour loads need no index load first.
+constexpr bool kGradNbShared = true;
+
 // Lifting order: false = directions 0, 1, 2 and a separate pass that forms the gradient record;
 // true = directions 1, 2, 0 with the record formed in the last sweep.
 constexpr bool kLiftFused = true;
@@ -319,18 +323,21 @@ struct NbIdx {
   int bf, tp;
 };
 
+// Where the neighbour data of own face point ln sit, from the face's (neighbour, face code) pair.
+template <int N>
+__device__ __forceinline__ NbIdx nb_index_of(int k, int c, int ln) {
+  NbIdx x;
+  x.bf = k >= 0 ? k * 6 + (c >> 3) : k;
+  x.tp = k >= 0 ? map_face_pt<N>(ln, c & 7) : 0;
+  return x;
+}
+
 template <int N, class R>
 __device__ __forceinline__ NbIdx nb_index(const KArgs<R>& A, int e, int F, int ln) {
-  NbIdx x;
+  // both words issued together (a wall's code entry is read and ignored)
   const int k = __ldg(A.m.nbr + e * 6 + F);
-  x.bf = k;
-  x.tp = 0;
-  if (k >= 0) {
-    const int c = __ldg(A.m.code + e * 6 + F);
-    x.bf = k * 6 + (c >> 3);
-    x.tp = map_face_pt<N>(ln, c & 7);
-  }
-  return x;
+  const int c = __ldg(A.m.code + e * 6 + F);
+  return nb_index_of<N>(k, c, ln);
 }
 
 template <int N, bool PERT, bool WANT_TV, class R>
@@ -384,8 +391,11 @@ struct FluxPre : FluxPreExtra<R, X> {
   NbIdx nbi[2];  // where the neighbour data of the two end points sit (modes 1, 2)
 };
 
+// snb: the element's six (neighbour, face code) pairs in shared memory, or null (read them from the
+// mesh tables).
 template <int N, bool PERT, class R, int D>
-__device__ __forceinline__ void lift_prefetch(const KArgs<R>& A, int e, int ln, LiftPre<N, R>& p) {
+__device__ __forceinline__ void lift_prefetch(const KArgs<R>& A, int e, int ln, LiftPre<N, R>& p,
+                                              const int* snb = nullptr) {
   constexpr int N2 = N * N, N3 = N * N * N;
   const R* Sl = A.m.Sf + ((size_t)e * 3 + D) * 3 * (N + 1) * N2;
 #pragma unroll
@@ -394,8 +404,13 @@ __device__ __forceinline__ void lift_prefetch(const KArgs<R>& A, int e, int ln, 
     for (int f = 0; f <= N; ++f) p.S[n][f] = __ldg(Sl + (n * (N + 1) + f) * N2 + ln);
 #pragma unroll
   for (int i = 0; i < N; ++i) p.ij[i] = __ldg(A.m.invJ + (size_t)e * N3 + line_pt<N, D>(ln, i));
-  p.nb[0] = load_nb<N, PERT, false>(A, e, 2 * D, ln);
-  p.nb[1] = load_nb<N, PERT, false>(A, e, 2 * D + 1, ln);
+  if (snb != nullptr) {
+    p.nb[0] = load_nb_at<N, PERT, false>(A, nb_index_of<N>(snb[4 * D], snb[4 * D + 1], ln));
+    p.nb[1] = load_nb_at<N, PERT, false>(A, nb_index_of<N>(snb[4 * D + 2], snb[4 * D + 3], ln));
+  } else {
+    p.nb[0] = load_nb<N, PERT, false>(A, e, 2 * D, ln);
+    p.nb[1] = load_nb<N, PERT, false>(A, e, 2 * D + 1, ln);
+  }
 }
 
 // How the flux sweep gets the neighbour data of its two end points: 0 = index and data loaded at
@@ -719,7 +734,7 @@ __device__ __forceinline__ void lift_dir(const KArgs<R>& A, R* sm, int el, int l
 // later direction's loads are issued before the barrier that precedes it.
 template <int N, bool PERT, class R, int EPB>
 __device__ __forceinline__ void lift_all(const KArgs<R>& A, R* sm, int el, int ln, int e, bool active,
-                                         LiftPre<N, R>& pre) {
+                                         LiftPre<N, R>& pre, const int* snb) {
   using L = Layout<N, PERT, R, EPB>;
   constexpr int N3 = N * N * N;
   if constexpr (kLiftFused) {
@@ -727,12 +742,12 @@ __device__ __forceinline__ void lift_all(const KArgs<R>& A, R* sm, int el, int l
     constexpr int d0 = lift_dir_at<N, R>(0), d1 = lift_dir_at<N, R>(1), d2 = lift_dir_at<N, R>(2);
     if (active) {
       lift_dir<N, PERT, R, EPB, d0, true, false>(A, sm, el, ln, e, pre);
-      lift_prefetch<N, PERT, R, d1>(A, e, ln, pre);
+      lift_prefetch<N, PERT, R, d1>(A, e, ln, pre, snb);
     }
     __syncthreads();
     if (active) {
       lift_dir<N, PERT, R, EPB, d1, false, false>(A, sm, el, ln, e, pre);
-      lift_prefetch<N, PERT, R, d2>(A, e, ln, pre);
+      lift_prefetch<N, PERT, R, d2>(A, e, ln, pre, snb);
     }
     __syncthreads();
     if (active) lift_dir<N, PERT, R, EPB, d2, false, true>(A, sm, el, ln, e, pre);
@@ -742,12 +757,12 @@ __device__ __forceinline__ void lift_all(const KArgs<R>& A, R* sm, int el, int l
   }
   if (active) {
     lift_dir<N, PERT, R, EPB, 0, true, false>(A, sm, el, ln, e, pre);
-    lift_prefetch<N, PERT, R, 1>(A, e, ln, pre);
+    lift_prefetch<N, PERT, R, 1>(A, e, ln, pre, snb);
   }
   __syncthreads();
   if (active) {
     lift_dir<N, PERT, R, EPB, 1, false, false>(A, sm, el, ln, e, pre);
-    lift_prefetch<N, PERT, R, 2>(A, e, ln, pre);
+    lift_prefetch<N, PERT, R, 2>(A, e, ln, pre, snb);
   }
   __syncthreads();
   if (active) lift_dir<N, PERT, R, EPB, 2, false, false>(A, sm, el, ln, e, pre);
@@ -1022,11 +1037,17 @@ __global__ void __launch_bounds__(EPB * N * N, sizeof(R) == 4 ? grad_min_blocks<
   fill_tables<N, R>(A.ops, sm + Layout<N, PERT, R, EPB>::oTAB);
   __syncthreads();
   LiftPre<N, R> pre;
+  // the six (neighbour, face code) pairs of each element, for the later directions' prefetches
+  __shared__ int snb[kGradNbShared ? EPB : 1][12];
   if (!stage_elements<N, PERT, R, EPB, false>(A, sm, &bar, ne, [&] {
         if (active) lift_prefetch<N, PERT, R, kLiftFused ? lift_dir_at<N, R>(0) : 0>(A, e, ln, pre);
+        if (kGradNbShared && active && ln < 6) {
+          snb[el][2 * ln] = __ldg(A.m.nbr + e * 6 + ln);
+          snb[el][2 * ln + 1] = __ldg(A.m.code + e * 6 + ln);
+        }
       }))
     return;
-  lift_all<N, PERT, R, EPB>(A, sm, el, ln, e, active, pre);
+  lift_all<N, PERT, R, EPB>(A, sm, el, ln, e, active, pre, kGradNbShared ? snb[kGradNbShared ? el : 0] : nullptr);
   // face metrics of the viscous-flux pass, loaded before the record stores
   R s3f[3][2][3];
   if (active && A.Tv_out != nullptr) {
