@@ -2,7 +2,7 @@
 // Elements per CTA: 2 (FP64 form); FP32 perturbation form: 5 (125 threads: three CTAs per SM fill 12
 // warps in both kernels; 4 elements left 28 of 128 lanes idle: the residual kernel ran 14 % slower,
 // the lifting kernel 24 % slower even at four CTAs per SM).
-// Tile 1 halves the FP32 elements per CTA (a candidate of the batched-shell autotuner).
+// Tile 1 (two elements per CTA) is the other candidate of the batched-shell autotuner.
 #include "kern_inst.cuh"
 
 namespace chorus {

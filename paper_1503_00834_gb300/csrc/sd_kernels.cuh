@@ -64,39 +64,29 @@ __device__ __forceinline__ int line_sidx(int ln, int s) {
   return sidx<N, R>(i, j, k);
 }
 
-// Residual-kernel options (FP32 perturbation form): whether the background line data are staged in
-// shared memory (else read through L1 per flux point), and the resident CTAs per SM asked of the
-// compiler (register cap) at N = 5.
+// Residual-kernel option (FP32 perturbation form): whether the background line data are staged in
+// shared memory (else read through L1 per flux point).
 constexpr bool kResidBgShared = true;
-constexpr int kResidMinBlocksF32 = 3;
-// Resident lifting CTAs asked for at N = 5 (five-element CTAs: three fit the shared memory; with
-// 168 registers a thread the lifting spills 28 bytes instead of 324 at the 128 of four CTAs).
-constexpr int kGradMinBlocksN5 = 3;
 // Whether the xi-line sweeps at N = 4 (FP32) read a line of the gradient record as one 16-byte
 // shared-memory load per component (the swizzled layout keeps a xi-line's 4 points contiguous).
 constexpr bool kVecGradLoad = true;
 
-// Per order, from timings of every combination on the 786,432-element p = 4 and the 98,304-element
-// p = 5 shells: the resident CTAs asked of the compiler for the residual and the lifting kernel, and
-// whether the flux sweep holds the line's gradient record in registers (else it reads it from
-// shared memory per flux point).  N = 6 runs two CTAs of four elements per SM (shared memory) and
-// does best with the registers that allows; N = 5 asks for three CTAs of each kernel, with the
-// gradient lines in shared memory.
-// At N = 3 and 4 the kernels ask for a number of warps per SM whatever their CTA size: 12 for the
-// residual kernel (168 registers a thread) and 16 for the lifting kernel (128); smaller CTAs at the
-// same warp count measured faster for the residual kernel (p = 3: four-element CTAs, six per SM,
-// 8 % faster than eight-element CTAs, three per SM; p = 2: seven-element CTAs 4.6 % faster than
-// fourteen-element ones), for the lifting kernel even at p = 3 and 1 % slower at p = 2.
+// Resident CTAs asked of the compiler (the register cap), from timings on the shells of every order:
+// the kernels ask for a number of warps per SM whatever their CTA size, 12 for the residual kernel
+// (~168 registers a thread) and 16 for the lifting kernel at N = 3, 4 (128), 12 at N = 5, 6.  Smaller
+// CTAs at the same warp count measured faster where their lanes stay full: the residual kernel at
+// p = 3 in four-element CTAs, six per SM (8 % faster than eight-element CTAs, three per SM), at p = 2
+// in seven-element ones (4.6 % faster than fourteen), at p = 5 in two-element ones, four per SM (5 %
+// faster than four-element CTAs, two per SM; the lifting kernel 3 %); at p = 4 the 25-thread
+// elements fill four warps only five to a CTA (two-element CTAs ran 14 % slower).  Shared memory
+// allows these counts at every order.  Also per order: whether the flux sweep holds the line's
+// gradient record in registers (else it reads it from shared memory per flux point).
 template <int N, int EPB>
 __host__ __device__ constexpr int warps_per_cta() { return (EPB * N * N + 31) / 32; }
 template <int N, int EPB>
-__host__ __device__ constexpr int resid_min_blocks() {
-  return N <= 4 ? 12 / warps_per_cta<N, EPB>() : N == 5 ? kResidMinBlocksF32 : 2;
-}
+__host__ __device__ constexpr int resid_min_blocks() { return 12 / warps_per_cta<N, EPB>(); }
 template <int N, int EPB>
-__host__ __device__ constexpr int grad_min_blocks() {
-  return N <= 4 ? 16 / warps_per_cta<N, EPB>() : N == 5 ? kGradMinBlocksN5 : 2;
-}
+__host__ __device__ constexpr int grad_min_blocks() { return (N <= 4 ? 16 : 12) / warps_per_cta<N, EPB>(); }
 template <int N>
 __host__ __device__ constexpr bool reg_grad_lines() { return N <= 4; }
 
