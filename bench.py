@@ -370,7 +370,7 @@ def run_batch(args, rank, world, local):
                        "orders": dict(Counter(b.orders)), "precision": "FP32 perturbation + FP64 background",
                        "step": "one SSP-RK3 step of every shell (captured graph, one launch per kernel and order)",
                        "tiles_elements_per_cta_p2_to_p5": choice, "dt": sh.dt,
-                       "orders_schedule": "concurrent streams" if b.schedule() else "one after another",
+                       "orders_schedule": ("one after another", "concurrent streams", "one persistent launch per stage")[b.schedule()],
                        "l2": "inputs larger than L2 (state %.0f MB)" % (state_bytes / 1e6),
                        "build_s": build_s, "parallelism": f"replicas x{world}"},
             "roofline": {"bound": "hbm", "kernel": "whole step (all kernels of all orders)", "achieved": achieved,

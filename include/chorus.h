@@ -314,8 +314,12 @@ chorus_status chorus_residual_noalloc(chorus_mesh mesh, const chorus_params* par
  * parameters; each has its own mesh, order and seeded perturbation.
  *  - Shells of one order form one internal mesh (their disjoint union), so each kernel of an RK
  *    stage is one launch per order present; the orders run concurrently on forked streams or one
- *    after another (chorus_batch_schedule; the autotuner picks the faster).  One RK step of the
- *    whole batch is captured once as a CUDA graph and replayed.
+ *    after another, and one RK step of the whole batch is captured once as a CUDA graph and
+ *    replayed.  A third schedule runs every order in one persistent cooperative launch per RK
+ *    stage: its CTAs take (order, tile) work items of each phase (traces, lifting, face fluxes,
+ *    residual; the orders' tiles in one list) from a counter and meet at bounded grid barriers
+ *    between the phases (a barrier that runs out of polls sets CHORUS_ETIMEOUT; nothing spins
+ *    unbounded).  chorus_batch_schedule sets it; the autotuner times all three.
  *  - State: FP32 perturbation form (CHORUS_FP32_PERT) only.  One caller-owned device array holds
  *    every shell; shell s occupies [state_offset[s], state_offset[s] + n_elem_s * 5 * N_s^3)
  *    floats, in the single-mesh layout of its own order.
@@ -351,8 +355,9 @@ chorus_status chorus_batch_layout(chorus_batch batch, int64_t* state_offset, int
 chorus_status chorus_batch_init(chorus_batch batch, float* Q, void* stream);
 
 /* n_steps SSP-RK3 steps of size dt for every shell.  The step graph is captured on the first call
- * for (Q, workspace, dt) and replayed; a call with other pointers or dt captures again.
- * launches: host int64 receiving the kernel launches per step, or NULL. */
+ * for (Q, workspace, dt) and replayed; a call with other pointers or dt captures again (the
+ * persistent schedule launches directly, three launches a step).  launches: host int64 receiving
+ * the kernel launches per step, or NULL. */
 chorus_status chorus_batch_rk_step(chorus_batch batch, float* Q, void* workspace, double dt, int64_t n_steps,
                                    void* stream, int64_t* launches);
 
@@ -363,14 +368,17 @@ chorus_status chorus_batch_reduce(chorus_batch batch, const float* Q, double* ou
 /* Autotuner: for each order, times n_trials RK steps with every built tile shape (elements per CTA)
  * of the FP32 kernels on this batch's own meshes and keeps the fastest; then times n_trials replays
  * of the captured step with the orders on concurrent streams and with the orders one after another,
- * keeps the faster schedule, and drops the captured graph.  Q and workspace are scratch (their
+ * and n_trials persistent steps where available, keeps the fastest schedule, and drops the
+ * captured graph.  Q and workspace are scratch (their
  * contents are overwritten).  choice: host int[4] receiving the chosen elements per CTA for
  * p = 2..5 (0 where the order is absent), or NULL.  Synchronises. */
 chorus_status chorus_batch_autotune(chorus_batch batch, float* Q, void* workspace, double dt, int n_trials,
                                     void* stream, int* choice);
 
 /* Schedule of the orders within a batch step: set 1 = concurrent streams, 0 = one after another,
- * any other value leaves it; concurrent: host int receiving the schedule in force, or NULL. */
+ * 2 = one persistent launch per RK stage (CHORUS_EUNSUPPORTED without cooperative launch or with a
+ * radial kappa_r(r)), any other value leaves it; concurrent: host int receiving the schedule in
+ * force (0, 1 or 2), or NULL. */
 chorus_status chorus_batch_schedule(chorus_batch batch, int set, int* concurrent);
 
 /* Well-balanced perturbation residual (FP32_PERT only; a library option the paper has no

@@ -20,7 +20,7 @@ INCLUDE = os.path.join(os.path.dirname(HERE), "include")
 
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 NVFLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-I", CSRC, "-I", INCLUDE]
-SOURCES = ["capi.cu", "batch.cu", "closure.cu", "closure_tc.cu", "kern_p2.cu", "kern_p3.cu", "kern_p4.cu", "kern_p5.cu", "mesh_builder.cpp"]
+SOURCES = ["capi.cu", "batch.cu", "batch_persist.cu", "closure.cu", "closure_tc.cu", "kern_p2.cu", "kern_p3.cu", "kern_p4.cu", "kern_p5.cu", "mesh_builder.cpp"]
 # Per-source options.  p = 3: the FP32 square roots (face normals, sound speeds, gravity) use the
 # approximate square root (the FP32 perturbation form's tolerance is 1e-5 relative; the FP64 kernels
 # are unaffected): 8 % faster there, slower at the other orders, which keep the IEEE square root.

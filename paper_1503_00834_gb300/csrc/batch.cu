@@ -1,9 +1,9 @@
 // Batched independent shells (declared in include/chorus.h): the shells of one order form one
 // mesh (their disjoint union: the face pairing joins only faces that share nodes, and the shells
-// share none), the orders run either concurrently on streams forked from the caller's stream or one
-// after another on it, one RK step of the whole batch is captured as a CUDA graph and replayed, and a
-// small autotuner picks the FP32 tile shape per order on the batch's own meshes and then the faster
-// of the two schedules.
+// share none).  Three schedules of an RK step: the orders concurrently on streams forked from the
+// caller's stream or one after another on it (both captured as a CUDA graph and replayed), or every
+// order in one persistent cooperative launch per RK stage (batch_persist.cu).  A small autotuner
+// picks the FP32 tile shape per order on the batch's own meshes and then the fastest schedule.
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -40,6 +40,8 @@ struct chorus_batch_s {
   cudaEvent_t fork = nullptr;
   cudaStream_t cap = nullptr;  // capture stream (the caller's may be the legacy stream, which cannot be captured)
   bool concurrent = true;  // orders on forked streams (true) or one after another (false)
+  bool persistent = false;  // one persistent launch per RK stage for all orders (overrides concurrent)
+  unsigned* d_sync = nullptr;  // the persistent launch's grid-barrier and work counters
   cudaGraphExec_t exec = nullptr;
   const float* g_Q = nullptr;
   const void* g_ws = nullptr;
@@ -67,6 +69,7 @@ void free_batch(chorus_batch_s* b) {
   }
   if (b->fork) cudaEventDestroy(b->fork);
   if (b->cap) cudaStreamDestroy(b->cap);
+  if (b->d_sync) cudaFree(b->d_sync);
   delete b;
 }
 
@@ -90,6 +93,30 @@ chorus_status step_all(chorus_batch_s* b, float* Q, void* ws, double dt, cudaStr
     if (cudaStreamWaitEvent(st, g.join, 0) != cudaSuccess) return CHORUS_ECUDA;
   }
   return CHORUS_OK;
+}
+
+// Whether the persistent schedule can run this batch: a device with cooperative launch, and no
+// radial radiative diffusivity (its kernel is built for a constant kappa_r).
+bool persistent_ok(const chorus_batch_s* b) {
+  return b->params.kappa_r1 == 0.0 && b->params.kappa_r2 == 0.0 && persist_grid() > 0;
+}
+
+// One RK step of every group as three persistent launches (one per SSP-RK3 stage).
+chorus_status step_persistent(chorus_batch_s* b, float* Q, void* ws, double dt, cudaStream_t st) {
+  if (!persistent_ok(b)) return CHORUS_EUNSUPPORTED;
+  if (!b->d_sync && cudaMalloc(&b->d_sync, 8 * sizeof(unsigned)) != cudaSuccess) {
+    b->d_sync = nullptr;
+    return CHORUS_ENOMEM;
+  }
+  StagePtrs sp[4];
+  StagePtrs* gp[4] = {nullptr, nullptr, nullptr, nullptr};
+  for (auto& g : b->groups) {
+    const int s = g.p - 2;
+    const chorus_status r = mesh_stage_ptrs(g.mesh, b->params, Q + g.state_off, (char*)ws + g.ws_off, &sp[s]);
+    if (r != CHORUS_OK) return r;
+    gp[s] = &sp[s];
+  }
+  return persist_rk3_step(gp, dt, b->d_sync, st);
 }
 
 chorus_status capture(chorus_batch_s* b, float* Q, void* ws, double dt) {
@@ -251,9 +278,17 @@ chorus_status chorus_batch_init(chorus_batch b, float* Q, void* stream) {
 chorus_status chorus_batch_rk_step(chorus_batch b, float* Q, void* workspace, double dt, int64_t n_steps,
                                    void* stream, int64_t* launches) {
   if (!b || !Q || !workspace || !(dt > 0.0) || !std::isfinite(dt) || n_steps < 0) return CHORUS_EINVAL;
-  if (launches) *launches = 10 * (int64_t)b->groups.size();  // per order: trace + 3 x (gradient, face, residual)
+  // per order: trace + 3 x (gradient, face, residual); persistent: one launch per stage
+  if (launches) *launches = b->persistent ? 3 : 10 * (int64_t)b->groups.size();
   if (n_steps == 0) return CHORUS_OK;
   cudaStream_t st = (cudaStream_t)stream;
+  if (b->persistent) {
+    for (int64_t n = 0; n < n_steps; ++n) {
+      const chorus_status s = step_persistent(b, Q, workspace, dt, st);
+      if (s != CHORUS_OK) return s;
+    }
+    return CHORUS_OK;
+  }
   if (!b->exec || b->g_Q != Q || b->g_ws != workspace || b->g_dt != dt) {
     // capturing runs nothing; the graph is launched on the caller's stream, which orders it
     const chorus_status s = capture(b, Q, workspace, dt);
@@ -324,8 +359,10 @@ chorus_status chorus_batch_autotune(chorus_batch b, float* Q, void* workspace, d
     const int epb = mesh_set_tile(g.mesh, best);
     if (choice) choice[g.p - 2] = epb;
   }
-  // then the schedule: the captured step with the orders concurrent and one after another
-  float sched_ms[2] = {0.0f, 0.0f};
+  // then the schedule: the captured step with the orders concurrent and one after another, and the
+  // persistent launches
+  float sched_ms[3] = {0.0f, 0.0f, 0.0f};
+  b->persistent = false;
   for (int c = 0; c < 2 && status == CHORUS_OK; ++c) {
     b->concurrent = c == 0;
     status = capture(b, Q, workspace, dt);
@@ -339,6 +376,15 @@ chorus_status chorus_batch_autotune(chorus_batch b, float* Q, void* workspace, d
   }
   b->concurrent = sched_ms[0] <= sched_ms[1];
   drop_graph(b);
+  if (status == CHORUS_OK && persistent_ok(b)) {
+    status = step_persistent(b, Q, workspace, dt, st);  // warm-up
+    if (status == CHORUS_OK && cudaEventRecord(t0, st) != cudaSuccess) status = CHORUS_ECUDA;
+    for (int n = 0; n < n_trials && status == CHORUS_OK; ++n) status = step_persistent(b, Q, workspace, dt, st);
+    if (status == CHORUS_OK && (cudaEventRecord(t1, st) != cudaSuccess || cudaEventSynchronize(t1) != cudaSuccess ||
+                                cudaEventElapsedTime(&sched_ms[2], t0, t1) != cudaSuccess))
+      status = CHORUS_ECUDA;
+    if (status == CHORUS_OK) b->persistent = sched_ms[2] < std::min(sched_ms[0], sched_ms[1]);
+  }
   cudaEventDestroy(t0);
   cudaEventDestroy(t1);
   return status;
@@ -346,11 +392,16 @@ chorus_status chorus_batch_autotune(chorus_batch b, float* Q, void* workspace, d
 
 chorus_status chorus_batch_schedule(chorus_batch b, int set, int* concurrent) {
   if (!b) return CHORUS_EINVAL;
+  if (set == 2 && !persistent_ok(b)) return CHORUS_EUNSUPPORTED;
   if (set == 0 || set == 1) {
     if (b->concurrent != (set == 1)) drop_graph(b);
     b->concurrent = set == 1;
+    b->persistent = false;
+  } else if (set == 2) {
+    drop_graph(b);
+    b->persistent = true;
   }
-  if (concurrent) *concurrent = b->concurrent ? 1 : 0;
+  if (concurrent) *concurrent = b->persistent ? 2 : b->concurrent ? 1 : 0;
   return CHORUS_OK;
 }
 

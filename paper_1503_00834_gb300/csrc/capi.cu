@@ -877,17 +877,7 @@ chorus_status chorus_residual(chorus_mesh m, const chorus_params* P, chorus_prec
 
 }  // extern "C"
 
-namespace {
-
-// One stage of an explicit SSP scheme: residual of `src`, fused combination into `dst` (and
-// optionally a second output), traces of `dst` for the next stage.
-struct Stage {
-  int src, dst;           // buffer ids: 0 u (the caller's state), 1 s, 2 A, 3 B
-  int un;                 // first extra input
-  double a, b, c;         // dst = a un + b src + c dt L(src)
-  int un2, out2;          // -1: none
-  double a2, b2, c2;      // out2 = a2 un2 + b2 src + c2 dt L(src)
-};
+namespace chorus {
 
 // SSP-RK3 (Shu-Osher) and SSP-RK(5,4) (Spiteri-Ruuth) stage lists
 const std::vector<Stage>& stages_of(int scheme) {
@@ -906,6 +896,10 @@ const std::vector<Stage>& stages_of(int scheme) {
   };
   return scheme == 1 ? rk54 : rk3;
 }
+
+}  // namespace chorus
+
+namespace {
 
 template <class R, class Grad, class Face, class Resid, class Trace>
 chorus_status run_rk(chorus_mesh_s* m, R* u, const Ws<R>& w, double dt, int64_t n_steps, int scheme, cudaStream_t st,
@@ -1445,6 +1439,29 @@ int mesh_set_tile(chorus_mesh_s* m, int tile) {
   m->L = launchers_for(m->p, tile);
   m->tile = tile;
   return m->L.epb32;
+}
+
+chorus_status mesh_stage_ptrs(chorus_mesh_s* m, const chorus_params& P, float* u, void* ws, StagePtrs* out) {
+  if (!m || !u || !ws || !out || !m->prepared || !same_params(m->prep, P)) return CHORUS_EINVAL;
+  const Ws<float> w = split_ws<float>(m, ws);
+  out->m = mesh_arg<float>(m);
+  out->ops = m->ops32;
+  out->ph = phys_arg<float>(P, m->r_inner, m->r_outer);
+  out->bg = bg_arg(m);
+  out->buf[0] = u;
+  out->buf[1] = w.s;
+  out->buf[2] = w.A;
+  out->buf[3] = w.B;
+  out->Ta = w.Ta;
+  out->Tb = w.Tb;
+  out->Tv = w.Tv;
+  out->G = w.G;
+  out->Fc = w.Fc;
+  out->faces = m->d_faces;
+  out->nf = m->n_ifaces;
+  out->nw = m->n_wfaces;
+  out->err = m->d_err;
+  return CHORUS_OK;
 }
 
 }  // namespace chorus

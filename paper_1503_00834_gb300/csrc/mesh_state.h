@@ -79,4 +79,39 @@ chorus_status mesh_reduce_range(chorus_mesh_s* m, const float* Q, int64_t e0, in
 // Select the FP32 tile shape `tile` (0 <= tile < n_tiles(p)); returns the elements per CTA or -1.
 int mesh_set_tile(chorus_mesh_s* m, int tile);
 
+// One stage of an explicit SSP scheme: residual of `src`, fused combination into `dst` (and
+// optionally a second output), traces of `dst` for the next stage.
+struct Stage {
+  int src, dst;           // buffer ids: 0 u (the caller's state), 1 s, 2 A, 3 B
+  int un;                 // first extra input
+  double a, b, c;         // dst = a un + b src + c dt L(src)
+  int un2, out2;          // -1: none
+  double a2, b2, c2;      // out2 = a2 un2 + b2 src + c2 dt L(src)
+};
+// Stage lists: scheme 0 SSP-RK3, 1 SSP-RK(5,4).
+const std::vector<Stage>& stages_of(int scheme);
+
+// The device arrays and constants of an FP32 RK stage of a prepared mesh, for the caller's state u
+// and workspace ws (the persistent batch step builds its kernel arguments from them).
+struct StagePtrs {
+  MeshArg<float> m;
+  OpsArg<float> ops;
+  PhysArg<float> ph;
+  BgArg bg;
+  float* buf[4];  // stage buffers: u, s, A, B (ids of Stage)
+  float *Ta, *Tb, *Tv, *G, *Fc;
+  const int2* faces;
+  int nf, nw;
+  unsigned* err;
+};
+chorus_status mesh_stage_ptrs(chorus_mesh_s* m, const chorus_params& P, float* u, void* ws, StagePtrs* out);
+
+// Persistent batch step (batch_persist.cu): one SSP-RK3 step of up to four order groups (slot
+// p - 2, null where the order is absent) as three cooperative launches, one per stage, each running
+// the stage's phases for every order with bounded grid barriers between them.  sync: 5 device words
+// of scratch.  CHORUS_EUNSUPPORTED when the device cannot launch it or a group has a radial kappa_r.
+chorus_status persist_rk3_step(StagePtrs* const groups[4], double dt, unsigned* sync, cudaStream_t st);
+// CTAs of the persistent launch (all resident at once), 0 when unavailable.
+int persist_grid();
+
 }  // namespace chorus

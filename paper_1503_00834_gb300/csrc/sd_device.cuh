@@ -50,27 +50,31 @@ __device__ __forceinline__ void bulk_s2g(void* dst, const void* src, uint32_t by
 __device__ __forceinline__ void bulk_commit() { asm volatile("cp.async.bulk.commit_group;" ::: "memory"); }
 // Wait until the committed bulk stores have read their shared-memory source (before the CTA exits).
 __device__ __forceinline__ void bulk_wait_read() { asm volatile("cp.async.bulk.wait_group.read 0;" ::: "memory"); }
+// Wait until the committed bulk stores have completed their writes to global memory.
+__device__ __forceinline__ void bulk_wait_all() { asm volatile("cp.async.bulk.wait_group 0;" ::: "memory"); }
 __device__ __forceinline__ void fence_async_smem() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
 
 // Polls of a bounded mbarrier wait when the mesh sets no limit of its own (about a second with the
 // back-off below).
 constexpr uint32_t kDefaultWaitPolls = 1u << 24;
 
-// Bounded wait on phase 0 of the barrier: at most `polls` polls.  Returns false if they ran out.
-__device__ __forceinline__ bool mbar_try0(uint64_t* bar, uint32_t polls) {
+// Bounded wait for the completion of the barrier's phase of the given parity (0 for a barrier's first
+// use): at most `polls` polls.  Returns false if they ran out.
+__device__ __forceinline__ bool mbar_try(uint64_t* bar, uint32_t parity, uint32_t polls) {
   const uint32_t a = smem_addr(bar);
   for (uint32_t it = 0; it < polls; ++it) {
     uint32_t ok;
     asm volatile(
-        "{ .reg .pred p; mbarrier.try_wait.parity.shared::cta.b64 p, [%1], 0; selp.b32 %0, 1, 0, p; }"
+        "{ .reg .pred p; mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2; selp.b32 %0, 1, 0, p; }"
         : "=r"(ok)
-        : "r"(a)
+        : "r"(a), "r"(parity)
         : "memory");
     if (ok) return true;
     if (it > 64) __nanosleep(64);
   }
   return false;
 }
+__device__ __forceinline__ bool mbar_try0(uint64_t* bar, uint32_t polls) { return mbar_try(bar, 0u, polls); }
 
 // The device control block of a mesh: err[0] error flags, err[1] the wait limit (0: the default,
 // k + 1: k polls).  Returns the number of polls of a kernel's staging waits.
@@ -83,11 +87,14 @@ __device__ __forceinline__ uint32_t wait_polls(const unsigned* err) {
 // Bounded wait for the bulk copies of a staging barrier.  If `polls` run out, sets bit 0 of *err
 // and waits once more (default limit) for the copies still in flight, so that no copy writes into
 // the shared memory of a CTA that has given up; returns false.
-__device__ __forceinline__ bool mbar_wait0(uint64_t* bar, unsigned* err, uint32_t polls) {
-  if (mbar_try0(bar, polls)) return true;
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, unsigned* err, uint32_t polls) {
+  if (mbar_try(bar, parity, polls)) return true;
   if (err) atomicOr(err, 1u);
-  mbar_try0(bar, kDefaultWaitPolls);
+  mbar_try(bar, parity, kDefaultWaitPolls);
   return false;
+}
+__device__ __forceinline__ bool mbar_wait0(uint64_t* bar, unsigned* err, uint32_t polls) {
+  return mbar_wait(bar, 0u, err, polls);
 }
 
 // ------------------------------------------------------------------ division

@@ -461,12 +461,14 @@ __device__ __forceinline__ R kr_at(const KArgs<R>& A, int e, int ln, int f) {
 
 // ------------------------------------------------------------------ trace kernel
 
+// Traces of tile `tile` (elements tile * EPB ...), one thread per (element, line); threads beyond
+// EPB * N^2 idle.
 template <int N, class R, int EPB>
-__global__ void __launch_bounds__(EPB * N * N) k_trace(const MeshArg<R> m, const OpsArg<R> ops, const R* __restrict__ q,
-                                                      R* __restrict__ T) {
+__device__ __forceinline__ void trace_tile(const MeshArg<R>& m, const OpsArg<R>& ops, const R* __restrict__ q,
+                                           R* __restrict__ T, int64_t tile) {
   constexpr int N2 = N * N, N3 = N * N * N;
   const int el = threadIdx.x / N2, ln = threadIdx.x % N2;
-  const int e = blockIdx.x * EPB + el;
+  const int64_t e = tile * EPB + el;
   if (el >= EPB || e >= m.E) return;
   const R* qe = q + (size_t)e * 5 * N3;
   R* Te = T + (size_t)e * 6 * 5 * N2;
@@ -487,6 +489,12 @@ __global__ void __launch_bounds__(EPB * N * N) k_trace(const MeshArg<R> m, const
     }
 }
 
+template <int N, class R, int EPB>
+__global__ void __launch_bounds__(EPB * N * N) k_trace(const MeshArg<R> m, const OpsArg<R> ops, const R* __restrict__ q,
+                                                      R* __restrict__ T) {
+  trace_tile<N, R, EPB>(m, ops, q, T, blockIdx.x);
+}
+
 // ------------------------------------------------------------------ staging
 
 // Bulk copy of element e's direction-d metrics S^d_n at the staged flux points (L::SF0 ..
@@ -505,15 +513,17 @@ __device__ __forceinline__ void stage_metric_block(const R* Sf, int64_t e, int d
   }
 }
 
-// `between` runs after the copies are issued and before the wait (it issues the first sweep's
-// global loads so that both latencies overlap).  Returns false, the same in every thread of the CTA,
-// when the bounded wait for the copies ran out (the flag is set in *A.err and the copies in flight
-// have been waited for): the caller then skips its computation and every global store.
+// Stages the elements e0 .. e0 + ne - 1.  `between` runs after the copies are issued and before the
+// wait (it issues the first sweep's global loads so that both latencies overlap).  The copies
+// complete the phase of `bar` whose parity is `parity` (flipped here whenever the barrier was used).
+// Returns false, the same in every thread of the CTA, when the bounded wait for the copies ran out
+// (the flag is set in *A.err and the copies in flight have been waited for): the caller then skips
+// its computation and every global store.
 template <int N, bool PERT, class R, int EPB, bool RES, class Between>
-__device__ __forceinline__ bool stage_elements(const KArgs<R>& A, R* sm, uint64_t* bar, int ne, Between&& between) {
+__device__ __forceinline__ bool stage_elements(const KArgs<R>& A, R* sm, uint64_t* bar, uint32_t& parity, int e0, int ne,
+                                               Between&& between) {
   using L = Layout<N, PERT, R, EPB, RES>;
   constexpr int N3 = N * N * N;
-  const int e0 = blockIdx.x * EPB;
   const bool tq = L::tmaQ && (((uintptr_t)A.q & 15u) == 0);
   const bool tb = L::bgShared && L::tmaBG && (((uintptr_t)A.bg.bg & 15u) == 0) && (((uintptr_t)A.bg.grho0 & 15u) == 0);
   const bool tg = A.G_in != nullptr && ((kG * N3 * sizeof(R)) % 16 == 0) && (((uintptr_t)A.G_in & 15u) == 0);
@@ -555,7 +565,10 @@ __device__ __forceinline__ bool stage_elements(const KArgs<R>& A, R* sm, uint64_
   const uint32_t polls = wait_polls(A.err);
   between();
   bool ok = true;
-  if (any_bulk) ok = mbar_wait0(bar, A.err, polls);
+  if (any_bulk) {
+    ok = mbar_wait(bar, parity, A.err, polls);
+    parity ^= 1u;
+  }
   return __syncthreads_and(ok) != 0;
 }
 
@@ -951,85 +964,84 @@ __device__ __forceinline__ void face_visc_dir(const KArgs<R>& A, const R* sm, in
 #pragma unroll
       for (int v = 0; v < 4; ++v) o[v * N2 + ln] = Fv[1 + v];
     }
-    return;
-  }
-  R qv[5][N], gv[kG][N], r0[N], E0l[N], g0[3][N];
+  } else {
+    R qv[5][N], gv[kG][N], r0[N], E0l[N], g0[3][N];
 #pragma unroll
-  for (int v = 0; v < 5; ++v) load_line_lin<N, D>(sq + v * N3, ln, qv[v]);
-  load_grad_lines<N, D>(sg, ln, gv);
-  if (PERT) {
-    load_line_bg<N, D>(sbg, ln, r0);
-    load_line_bg<N, D>(sbg + N3, ln, E0l);
-#pragma unroll
-    for (int n = 0; n < 3; ++n) load_line_bg<N, D>(sgr0 + n * N3, ln, g0[n]);
-  }
-#pragma unroll 1
-  for (int side = 0; side < 2; ++side) {
-    const int f = side ? N : 0;
-    const int kind = kFaceKernel ? __ldg(A.m.nbr + e * 6 + 2 * D + side) : 0;
-    R w[N];
-#pragma unroll
-    for (int s = 0; s < N; ++s) w[s] = tI[f * N + s];
-    R qf[5], gf[kG], gr0f[3] = {R(0), R(0), R(0)};
-    R rho0f = R(0), E0f = R(0);
-#pragma unroll
-    for (int v = 0; v < 5; ++v) {
-      qf[v] = R(0);
-#pragma unroll
-      for (int s = 0; s < N; ++s) qf[v] += w[s] * qv[v][s];
-    }
-#pragma unroll
-    for (int c = 0; c < kG; ++c) {
-      gf[c] = R(0);
-#pragma unroll
-      for (int s = 0; s < N; ++s) gf[c] += w[s] * gv[c][s];
-    }
+    for (int v = 0; v < 5; ++v) load_line_lin<N, D>(sq + v * N3, ln, qv[v]);
+    load_grad_lines<N, D>(sg, ln, gv);
     if (PERT) {
+      load_line_bg<N, D>(sbg, ln, r0);
+      load_line_bg<N, D>(sbg + N3, ln, E0l);
 #pragma unroll
-      for (int s = 0; s < N; ++s) {
-        rho0f += w[s] * r0[s];
-        E0f += w[s] * E0l[s];
-#pragma unroll
-        for (int n = 0; n < 3; ++n) gr0f[n] += w[s] * g0[n][s];
-      }
+      for (int n = 0; n < 3; ++n) load_line_bg<N, D>(sgr0 + n * N3, ln, g0[n]);
     }
-    R s3[3];
+#pragma unroll 1
+    for (int side = 0; side < 2; ++side) {
+      const int f = side ? N : 0;
+      const int kind = kFaceKernel ? __ldg(A.m.nbr + e * 6 + 2 * D + side) : 0;
+      R w[N];
 #pragma unroll
-    for (int n = 0; n < 3; ++n) s3[n] = side ? s3f[1][n] : s3f[0][n];
-    const R sgn = side ? R(1) : R(-1);
-    const R mag = sqrt(s3[0] * s3[0] + s3[1] * s3[1] + s3[2] * s3[2]);
-    const R im = qdiv(sgn, mag);
-    const R nh[3] = {im * s3[0], im * s3[1], im * s3[2]};
-    const Pt<R> st = point_state<PERT>(qf, rho0f, E0f, A.ph);
-    const R krf = kr_at<N, D, KR>(A, e, ln, f);
-    R Fv[5];
-    flux_visc<PERT>(st, gf, gr0f, rho0f, A.ph.gm1 * E0f, nh, A.ph, krf, Fv);
-    if (kFaceKernel && kind < 0) Fv[4] = wall_conduction(gf, nh, krf, A.ph);
-    R* o = A.Tv_out + ((size_t)e * 6 + 2 * D + side) * 4 * N2;
+      for (int s = 0; s < N; ++s) w[s] = tI[f * N + s];
+      R qf[5], gf[kG], gr0f[3] = {R(0), R(0), R(0)};
+      R rho0f = R(0), E0f = R(0);
 #pragma unroll
-    for (int v = 0; v < 4; ++v) o[v * N2 + ln] = Fv[1 + v];
+      for (int v = 0; v < 5; ++v) {
+        qf[v] = R(0);
+#pragma unroll
+        for (int s = 0; s < N; ++s) qf[v] += w[s] * qv[v][s];
+      }
+#pragma unroll
+      for (int c = 0; c < kG; ++c) {
+        gf[c] = R(0);
+#pragma unroll
+        for (int s = 0; s < N; ++s) gf[c] += w[s] * gv[c][s];
+      }
+      if (PERT) {
+#pragma unroll
+        for (int s = 0; s < N; ++s) {
+          rho0f += w[s] * r0[s];
+          E0f += w[s] * E0l[s];
+#pragma unroll
+          for (int n = 0; n < 3; ++n) gr0f[n] += w[s] * g0[n][s];
+        }
+      }
+      R s3[3];
+#pragma unroll
+      for (int n = 0; n < 3; ++n) s3[n] = side ? s3f[1][n] : s3f[0][n];
+      const R sgn = side ? R(1) : R(-1);
+      const R mag = sqrt(s3[0] * s3[0] + s3[1] * s3[1] + s3[2] * s3[2]);
+      const R im = qdiv(sgn, mag);
+      const R nh[3] = {im * s3[0], im * s3[1], im * s3[2]};
+      const Pt<R> st = point_state<PERT>(qf, rho0f, E0f, A.ph);
+      const R krf = kr_at<N, D, KR>(A, e, ln, f);
+      R Fv[5];
+      flux_visc<PERT>(st, gf, gr0f, rho0f, A.ph.gm1 * E0f, nh, A.ph, krf, Fv);
+      if (kFaceKernel && kind < 0) Fv[4] = wall_conduction(gf, nh, krf, A.ph);
+      R* o = A.Tv_out + ((size_t)e * 6 + 2 * D + side) * 4 * N2;
+#pragma unroll
+      for (int v = 0; v < 4; ++v) o[v * N2 + ln] = Fv[1 + v];
+    }
   }
 }
 
-// FP32: 16 resident warps per SM at N = 3, 4 (register cap 128), as grad_min_blocks gives
+// Lifting of tile `tile` (elements tile * EPB ...; threads beyond EPB * N^2 idle but take part in the
+// barriers).  bar: the CTA's staging barrier (initialised), pbar: the parity of its next phase.
 template <int N, bool PERT, class R, int EPB, bool KR>
-__global__ void __launch_bounds__(EPB * N * N, sizeof(R) == 4 ? grad_min_blocks<N, EPB>() : 1) k_grad(const KArgs<R> A) {
+__device__ __forceinline__ void grad_tile(const KArgs<R>& A, int64_t tile, uint64_t* bar, uint32_t& pbar) {
   constexpr int N2 = N * N;
   extern __shared__ __align__(128) unsigned char smem_raw[];
-  __shared__ __align__(8) uint64_t bar;
   R* sm = reinterpret_cast<R*>(smem_raw);
   const int el = threadIdx.x / N2, ln = threadIdx.x % N2;
-  const int e0 = blockIdx.x * EPB;
+  const int e0 = (int)(tile * EPB);
   const int ne = min(EPB, A.m.E - e0);
   const int e = e0 + el;
   const bool active = el < ne;
-  if (threadIdx.x == 0) mbar_init(&bar);
   fill_tables<N, R>(A.ops, sm + Layout<N, PERT, R, EPB>::oTAB);
   __syncthreads();
   LiftPre<N, R> pre;
   // the six (neighbour, face code) pairs of each element, for the later directions' prefetches
   __shared__ int snb[kGradNbShared ? EPB : 1][12];
-  if (!stage_elements<N, PERT, R, EPB, false>(A, sm, &bar, ne, [&] {
+  if (!stage_elements<N, PERT, R, EPB, false>(A, sm, bar, pbar, e0, ne, [&] {
         if (active) lift_prefetch<N, PERT, R, kLiftFused ? lift_dir_at<N, R>(0) : 0>(A, e, ln, pre);
         if (kGradNbShared && active && ln < 6) {
           snb[el][2 * ln] = __ldg(A.m.nbr + e * 6 + ln);
@@ -1071,6 +1083,15 @@ __global__ void __launch_bounds__(EPB * N * N, sizeof(R) == 4 ? grad_min_blocks<
     face_visc_dir<N, PERT, R, EPB, 2, KR>(A, sm, el, ln, e, s3f[2]);
   }
   if (g_bulk && threadIdx.x == 0) bulk_wait_read();  // the CTA's shared memory must outlive the reads
+}
+
+// FP32: 16 resident warps per SM at N = 3, 4 (register cap 128), as grad_min_blocks gives
+template <int N, bool PERT, class R, int EPB, bool KR>
+__global__ void __launch_bounds__(EPB * N * N, sizeof(R) == 4 ? grad_min_blocks<N, EPB>() : 1) k_grad(const KArgs<R> A) {
+  __shared__ __align__(8) uint64_t bar;
+  if (threadIdx.x == 0) mbar_init(&bar);  // ordered by the tile's first barrier
+  uint32_t ph = 0;
+  grad_tile<N, PERT, R, EPB, KR>(A, blockIdx.x, &bar, ph);
 }
 
 // ------------------------------------------------------------------ flux sweep, one direction
@@ -1289,27 +1310,21 @@ __device__ __forceinline__ void flux_dir(const KArgs<R>& A, R* sm, int el, int l
 
 // ------------------------------------------------------------------ residual kernel
 
-// FP32: 12 resident warps per SM at N = 3, 4 (register cap ~168 per thread), as resid_min_blocks gives
+// Residual (and RK stage) of tile `tile` (elements tile * EPB ...; threads beyond EPB * N^2 idle but
+// take part in the barriers).  bar: the staging barrier, barS: the two staged-metric barriers (used
+// when L::SM; all initialised), pbar / pbarS: the parities of their next phases.
 template <int N, bool PERT, class R, int EPB, int MODE, bool KR>
-__global__ void __launch_bounds__(EPB * N * N, sizeof(R) == 4 ? resid_min_blocks<N, EPB>() : 1) k_resid(const KArgs<R> A) {
+__device__ __forceinline__ void resid_tile(const KArgs<R>& A, int64_t tile, uint64_t* bar, uint64_t* barS,
+                                           uint32_t& pbar, uint32_t& pbarS) {
   using L = Layout<N, PERT, R, EPB, true>;
   constexpr int N2 = N * N, N3 = N * N * N;
   extern __shared__ __align__(128) unsigned char smem_raw[];
-  __shared__ __align__(8) uint64_t bar;
-  __shared__ __align__(8) uint64_t barS[L::SM ? 2 : 1];  // staged metrics of directions 1 and 2
   R* sm = reinterpret_cast<R*>(smem_raw);
   const int el = threadIdx.x / N2, ln = threadIdx.x % N2;
-  const int e0 = blockIdx.x * EPB;
+  const int e0 = (int)(tile * EPB);
   const int ne = min(EPB, A.m.E - e0);
   const int e = e0 + el;
   const bool active = el < ne;
-  if (threadIdx.x == 0) {
-    mbar_init(&bar);
-    if constexpr (L::SM) {
-      mbar_init(&barS[0]);
-      mbar_init(&barS[1]);
-    }
-  }
   fill_tables<N, R>(A.ops, sm + L::oTAB);
   __syncthreads();
   // direction d's metric blocks of the CTA's elements into buffer `buf` (thread 0), on barrier b
@@ -1328,7 +1343,7 @@ __global__ void __launch_bounds__(EPB * N * N, sizeof(R) == 4 ? resid_min_blocks
   bool failed = false;
   FluxPre<R, !stage_metrics<N, R>() && ((N == 4 && kEndFirstD0) || s3_ahead<N>() == 2)> fp;
   __shared__ int snb[flux_nb_mode<N>() == 3 ? EPB : 1][12];  // (neighbour, face code) of the 6 faces
-  if (!stage_elements<N, PERT, R, EPB, true>(A, sm, &bar, ne, [&] {
+  if (!stage_elements<N, PERT, R, EPB, true>(A, sm, bar, pbar, e0, ne, [&] {
         if (active) flux_prefetch<N, PERT, R, 0>(A, e, ln, fp);
         if (!kFaceKernel && flux_nb_mode<N>() == 3 && active && ln < 6) {
           snb[el][2 * ln] = __ldg(A.m.nbr + e * 6 + ln);
@@ -1345,13 +1360,16 @@ __global__ void __launch_bounds__(EPB * N * N, sizeof(R) == 4 ? resid_min_blocks
   }
   __syncthreads();
   stage_dir(2, 0, &barS[1]);
-  if constexpr (L::SM) failed |= !mbar_wait0(&barS[0], A.err, polls);
+  if constexpr (L::SM) failed |= !mbar_wait(&barS[0], pbarS, A.err, polls);
   if (active) {
     flux_dir<N, PERT, R, EPB, 1, KR>(A, sm, el, ln, e, fp, snb_el, sS1);
     flux_prefetch<N, PERT, R, 2>(A, e, ln, fp);
   }
   __syncthreads();
-  if constexpr (L::SM) failed |= !mbar_wait0(&barS[1], A.err, polls);
+  if constexpr (L::SM) {
+    failed |= !mbar_wait(&barS[1], pbarS, A.err, polls);
+    pbarS ^= 1u;  // both staged-metric barriers completed a phase
+  }
   if (active) flux_dir<N, PERT, R, EPB, 2, KR>(A, sm, el, ln, e, fp, snb_el, sS0);
 
   // Global inputs of the epilogue, all issued before its first store.  The epilogue works point by
@@ -1440,6 +1458,22 @@ __global__ void __launch_bounds__(EPB * N * N, sizeof(R) == 4 ? resid_min_blocks
   }
 }
 
+// FP32: 12 resident warps per SM at N = 3, 4 (register cap ~168 per thread), as resid_min_blocks gives
+template <int N, bool PERT, class R, int EPB, int MODE, bool KR>
+__global__ void __launch_bounds__(EPB * N * N, sizeof(R) == 4 ? resid_min_blocks<N, EPB>() : 1) k_resid(const KArgs<R> A) {
+  __shared__ __align__(8) uint64_t bar;
+  __shared__ __align__(8) uint64_t barS[2];  // staged metrics of directions 1 and 2
+  if (threadIdx.x == 0) {  // ordered by the tile's first barrier
+    mbar_init(&bar);
+    if constexpr (Layout<N, PERT, R, EPB, true>::SM) {
+      mbar_init(&barS[0]);
+      mbar_init(&barS[1]);
+    }
+  }
+  uint32_t ph = 0, phS = 0;
+  resid_tile<N, PERT, R, EPB, MODE, KR>(A, blockIdx.x, &bar, barS, ph, phS);
+}
+
 // ------------------------------------------------------------------ face kernel
 
 // Common flux of every interior face point, once per face (Section 3: Rusanov inviscid flux with the
@@ -1452,11 +1486,11 @@ __global__ void __launch_bounds__(EPB * N * N, sizeof(R) == 4 ? resid_min_blocks
 // Wall faces follow the interior ones in the list (entries nf..nf+nw-1): their common flux (Section 5)
 // is formed from the element's own trace and the lifting kernel's wall data (the viscous traction
 // tau n and the conductive flux with the top temperature imposed).
+// One thread's face point g (of (nf + nw) * N^2).
 template <int N, bool PERT, class R>
-__global__ void __launch_bounds__(64) k_face(const KArgs<R> A, const int2* __restrict__ faces, int nf, int nw) {
+__device__ __forceinline__ void face_point(const KArgs<R>& A, const int2* __restrict__ faces, int nf, int nw, int64_t g) {
   constexpr int N2 = N * N;
-  const int64_t g = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-  if (g >= (int64_t)(nf + nw) * N2) return;
+  if (g < 0 || g >= (int64_t)(nf + nw) * N2) return;
   const int t = (int)(g % N2);
   const int2 fc = faces[g / N2];
   const int e = fc.x, F = fc.y, D = F >> 1, side = F & 1;
@@ -1533,6 +1567,11 @@ __global__ void __launch_bounds__(64) k_face(const KArgs<R> A, const int2* __res
     A.Fc_out[(oL * 5 + v) * N2 + t] = sgn * mag * Fh[v];
     A.Fc_out[(oR * 5 + v) * N2 + tp] = -sR_ * mag * Fh[v];
   }
+}
+
+template <int N, bool PERT, class R>
+__global__ void __launch_bounds__(64) k_face(const KArgs<R> A, const int2* __restrict__ faces, int nf, int nw) {
+  face_point<N, PERT, R>(A, faces, nf, nw, blockIdx.x * (int64_t)blockDim.x + threadIdx.x);
 }
 
 // ------------------------------------------------------------------ launch helpers

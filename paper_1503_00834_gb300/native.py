@@ -349,12 +349,15 @@ class Batch:
         _ok("chorus_batch_reduce", load().chorus_batch_reduce(self.handle, _ptr(Q), out, _stream(stream)))
         return np.array(out[:]).reshape(-1, 4)
 
-    def schedule(self, concurrent=None) -> bool:
-        """The schedule of the orders in a step (True: concurrent streams); sets it when given."""
+    SERIAL, CONCURRENT, PERSISTENT = 0, 1, 2
+
+    def schedule(self, mode=None) -> int:
+        """The schedule of a step: 0 the orders one after another, 1 on concurrent streams (a bool
+        means 1 / 0), 2 one persistent launch per RK stage; sets it when given, returns the one in force."""
         out = ctypes.c_int()
-        set_ = -1 if concurrent is None else (1 if concurrent else 0)
+        set_ = -1 if mode is None else int(mode)
         _ok("chorus_batch_schedule", load().chorus_batch_schedule(self.handle, set_, ctypes.byref(out)))
-        return bool(out.value)
+        return out.value
 
     def autotune(self, Q, ws, dt: float, n_trials: int = 3, stream=None):
         """Chosen elements per CTA for p = 2..5 (0 where absent)."""

@@ -143,21 +143,29 @@ def test_autotune_picks_a_built_tile_and_keeps_results(batch):
         assert d <= 1e-6 * scale
 
 
-def test_both_schedules_give_the_same_shells(batch):
-    """The orders one after another or on concurrent streams: the same kernels on disjoint data, so
-    every shell's state is bit-identical after three steps."""
+def test_all_schedules_give_the_same_shells(batch):
+    """The orders one after another or on concurrent streams (the same kernels on disjoint data):
+    every shell's state is bit-identical after three steps.  One persistent launch per RK stage runs
+    the same per-element arithmetic compiled into another kernel (where the compiler may fuse other
+    products into FMAs): within 1e-6 of the state's scale, and three launches a step."""
     b = batch.batch
     was = b.schedule()
     try:
         out = []
-        for concurrent in (True, False):
-            assert b.schedule(concurrent) == concurrent
+        for mode in (b.CONCURRENT, b.SERIAL, b.PERSISTENT):
+            assert b.schedule(mode) == mode
             Q, ws = _alloc(batch)
             b.init(Q)
-            b.rk_step(Q, ws, batch.dt, 3)
+            launches = b.rk_step(Q, ws, batch.dt, 3)
             torch.cuda.synchronize()
+            assert np.all(np.isfinite(b.reduce(Q)))  # also reports a flag a wait set
+            assert launches == (3 if mode == b.PERSISTENT else 10 * len({c.p for c in batch.cfgs})), (mode, launches)
             out.append(Q)
         for s in range(len(batch.cfgs)):
             assert torch.equal(b.view(out[0], s), b.view(out[1], s)), s
+            q, p = b.view(out[0], s), b.view(out[2], s)
+            d, scale = (q - p).abs().max().item(), q.abs().max().item()
+            print(f"shell {s}: max |persistent - serial| = {d:.3e} (scale {scale:.3e})")
+            assert d <= 1e-6 * scale, s
     finally:
         b.schedule(was)
