@@ -381,6 +381,11 @@ chorus_status chorus_batch_autotune(chorus_batch batch, float* Q, void* workspac
  * force (0, 1 or 2), or NULL. */
 chorus_status chorus_batch_schedule(chorus_batch batch, int set, int* concurrent);
 
+/* chorus_set_wait_limit on every mesh of the batch.  The persistent schedule's grid barriers poll
+ * with the same limit (0: a barrier gives up at once, sets the error flag, and the launch ends
+ * without computing; chorus_batch_reduce then reports CHORUS_ETIMEOUT).  Synchronous. */
+chorus_status chorus_batch_set_wait_limit(chorus_batch batch, int64_t polls);
+
 /* Well-balanced perturbation residual (FP32_PERT only; a library option the paper has no
  * counterpart for).  The residual of Q0 + q' becomes R(Q0 + q') - R(Q0): the discrete residual of the
  * polytropic background at rest, which is not zero but of truncation size (the discretised

@@ -390,6 +390,15 @@ chorus_status chorus_batch_autotune(chorus_batch b, float* Q, void* workspace, d
   return status;
 }
 
+chorus_status chorus_batch_set_wait_limit(chorus_batch b, int64_t polls) {
+  if (!b) return CHORUS_EINVAL;
+  for (auto& g : b->groups) {
+    const chorus_status s = chorus_set_wait_limit(g.mesh, polls);
+    if (s != CHORUS_OK) return s;
+  }
+  return CHORUS_OK;
+}
+
 chorus_status chorus_batch_schedule(chorus_batch b, int set, int* concurrent) {
   if (!b) return CHORUS_EINVAL;
   if (set == 2 && !persistent_ok(b)) return CHORUS_EUNSUPPORTED;

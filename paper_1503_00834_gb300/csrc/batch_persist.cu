@@ -28,8 +28,7 @@ struct PersistArgs {
   int64_t items[4][4];  // [phase: traces, lifting, faces, residual][slot]
   int trace;            // 1: the stage starts with the traces of its input state
   unsigned* sync;       // [0] grid-barrier arrivals, [1 + phase] work counter (zero at launch)
-  unsigned* err;        // error flags: bit 0 a bounded wait gave up
-  uint32_t polls;       // poll limit of a grid barrier
+  unsigned* err;        // the error flags (bit 0: a bounded wait gave up) and, in err[1], the wait limit
 };
 static_assert(sizeof(PersistArgs) <= 32000, "kernel parameters above the 32 KB limit");
 
@@ -106,6 +105,7 @@ __global__ void __launch_bounds__(kPThreads, kPMinBlocks) k_batch_stage(const __
   __syncthreads();
   uint32_t pbar = 0, pbarS = 0;
   unsigned barriers = 0;
+  const uint32_t polls = wait_polls(P.err);  // the grid barriers' limit: the staging waits' own
   for (int phase = P.trace ? 0 : 1; phase < 4; ++phase) {
     const int64_t total = P.items[phase][0] + P.items[phase][1] + P.items[phase][2] + P.items[phase][3];
     for (;;) {
@@ -129,7 +129,7 @@ __global__ void __launch_bounds__(kPThreads, kPMinBlocks) k_batch_stage(const __
       if (threadIdx.x == 0 && (*(volatile unsigned*)P.err & 1u)) s_stop = 1;  // a bounded wait gave up
     }
     if (phase == 1 && threadIdx.x == 0) bulk_wait_all();  // the gradient records are written out
-    if (phase < 3 && !grid_sync(P.sync, ++barriers * gridDim.x, P.err, P.polls)) return;
+    if (phase < 3 && !grid_sync(P.sync, ++barriers * gridDim.x, P.err, polls)) return;
   }
 }
 
@@ -213,7 +213,6 @@ chorus_status persist_rk3_step(StagePtrs* const groups[4], double dt, unsigned* 
     P.trace = k == 0;
     P.sync = sync;
     P.err = err;
-    P.polls = kDefaultWaitPolls;
     if (cudaMemsetAsync(sync, 0, 5 * sizeof(unsigned), st) != cudaSuccess) return CHORUS_ECUDA;
     void* args[] = {&P};
     if (cudaLaunchCooperativeKernel((const void*)k_batch_stage, dim3(grid), dim3(kPThreads), args, kPSmem, st) !=

@@ -31,7 +31,8 @@ EXPORTS = ("chorus_mesh_create", "chorus_mesh_destroy", "chorus_mesh_info", "cho
            "chorus_batch_destroy", "chorus_batch_layout", "chorus_batch_init", "chorus_batch_rk_step",
            "chorus_batch_reduce", "chorus_batch_autotune", "chorus_set_well_balanced", "chorus_prepare_profile",
            "chorus_afb_profile", "chorus_closure_set_scales", "chorus_stable_dt_rule", "chorus_stable_dt",
-           "chorus_set_wait_limit", "chorus_fma_rate", "chorus_rk_step_host", "chorus_batch_schedule")
+           "chorus_set_wait_limit", "chorus_fma_rate", "chorus_rk_step_host", "chorus_batch_schedule",
+           "chorus_batch_set_wait_limit")
 
 
 class ChorusError(RuntimeError):
@@ -124,6 +125,7 @@ def load() -> ctypes.CDLL:
         "chorus_fma_rate": (i32, [i32, vp, P(f64)]),
         "chorus_rk_step_host": (i32, [vp, P(Params), i32, vp, vp, vp, f64, i64, vp]),
         "chorus_batch_schedule": (i32, [vp, i32, P(i32)]),
+        "chorus_batch_set_wait_limit": (i32, [vp, i64]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(lib, name)
@@ -350,6 +352,10 @@ class Batch:
         return np.array(out[:]).reshape(-1, 4)
 
     SERIAL, CONCURRENT, PERSISTENT = 0, 1, 2
+
+    def set_wait_limit(self, polls: int) -> None:
+        """Polls of the bounded staging waits and grid barriers of every mesh (negative: the default)."""
+        _ok("chorus_batch_set_wait_limit", load().chorus_batch_set_wait_limit(self.handle, polls))
 
     def schedule(self, mode=None) -> int:
         """The schedule of a step: 0 the orders one after another, 1 on concurrent streams (a bool

@@ -169,3 +169,37 @@ def test_all_schedules_give_the_same_shells(batch):
             assert d <= 1e-6 * scale, s
     finally:
         b.schedule(was)
+
+
+def test_persistent_barrier_timeout_is_reported_and_stores_nothing(batch):
+    """The persistent schedule's bounded waits, made to run out: with a wait limit of zero polls the
+    first grid barrier (or staging wait) of every launch gives up at once, the CTAs stop, nothing of
+    the state is written, and the batch reduction reports CHORUS_ETIMEOUT once; with the default
+    limit again the same step gives the normal result.  Nothing spins unbounded."""
+    from paper_1503_00834_gb300 import ChorusError
+
+    b = batch.batch
+    was = b.schedule()
+    try:
+        b.schedule(b.PERSISTENT)
+        Q, ws = _alloc(batch)
+        b.init(Q)
+        Q0 = Q.clone()
+        try:
+            b.set_wait_limit(0)
+            b.rk_step(Q, ws, batch.dt, 1)
+            torch.cuda.synchronize()
+            with pytest.raises(ChorusError) as e:
+                b.reduce(Q)
+            assert e.value.status == 6  # CHORUS_ETIMEOUT
+        finally:
+            b.set_wait_limit(-1)
+        assert torch.equal(Q, Q0)  # the launches that gave up wrote nothing of the state
+        b.rk_step(Q, ws, batch.dt, 1)
+        assert np.all(np.isfinite(b.reduce(Q)))  # reported once, then cleared
+        Q1 = Q.clone()
+        b.init(Q)
+        b.rk_step(Q, ws, batch.dt, 1)
+        assert torch.equal(Q, Q1) and not torch.equal(Q1, Q0)
+    finally:
+        b.schedule(was)
