@@ -7,11 +7,13 @@ time step = 3 passes of the whole residual + stage update; the metric counts sol
 updates per stage (DOF = elements x N^3, Eq. 19).
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl chorus|reference] [--prec fp32|fp64]
-                  [--workload batch_64]
+                  [--workload batch_64|batch_16] [--schedule auto|serial|concurrent|persistent]
 
 --workload batch_64 times the batch of 64 independent shells (orders 2-5, uneven sizes, 176M
-solution points) advanced together: per-order union meshes, forked streams, a captured step graph,
-tile shapes from the autotuner.
+solution points) advanced together: per-order union meshes, a captured step graph (the orders one
+after another or on forked streams) or one persistent launch per stage, tile shapes and schedule
+from the autotuner (--schedule overrides the schedule); batch_16 is the same family at a quarter of
+the size.
 
 --impl reference times the plain FP64 CPU oracle (the only reference implementation: the paper
 ships no code) on the host cores, on a bounded sample of the same workload.
@@ -298,8 +300,9 @@ def run_batch(args, rank, world, local):
     """Batched independent shells: K graph-replayed SSP-RK3 steps of the whole batch."""
     import torch
 
-    from chorus_inputs import BATCH_64
+    from chorus_inputs import BATCH_16, BATCH_64
 
+    bcfg = {"batch_64": BATCH_64, "batch_16": BATCH_16}[args.workload]
     torch.cuda.set_device(local)
     if world > 1:
         import torch.distributed as dist
@@ -310,12 +313,14 @@ def run_batch(args, rank, world, local):
     _build.build()
     stream = torch.cuda.current_stream()
     t0 = time.perf_counter()
-    sh = Shells(BATCH_64)
+    sh = Shells(bcfg)
     b = sh.batch
     build_s = time.perf_counter() - t0
     Q = torch.empty(b.n_state, dtype=torch.float32, device="cuda")
     ws = torch.empty(b.workspace_bytes, dtype=torch.uint8, device="cuda")
     choice = b.autotune(Q, ws, sh.dt, n_trials=2)
+    if args.schedule != "auto":  # the tiles stay the autotuner's
+        b.schedule({"serial": b.SERIAL, "concurrent": b.CONCURRENT, "persistent": b.PERSISTENT}[args.schedule])
     b.init(Q)
     launches = b.rk_step(Q, ws, sh.dt, max(3, args.warmup))
     torch.cuda.synchronize()
@@ -366,9 +371,11 @@ def run_batch(args, rank, world, local):
             "metric": "RK-stage DOF updates/s, batch of independent shells", "value": value, "unit": UNIT,
             "n_gpus": world, "steps": args.steps, "warmup": max(3, args.warmup), "ms_per_step": ms / args.steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-            "config": {"workload": BATCH_64.name, "shells": len(sh.cfgs), "elements": sum(b.n_elem), "dof": n_dof,
+            "config": {"workload": bcfg.name, "shells": len(sh.cfgs), "elements": sum(b.n_elem), "dof": n_dof,
                        "orders": dict(Counter(b.orders)), "precision": "FP32 perturbation + FP64 background",
-                       "step": "one SSP-RK3 step of every shell (captured graph, one launch per kernel and order)",
+                       "step": "one SSP-RK3 step of every shell (" + (
+                           "one persistent launch per stage" if b.schedule() == b.PERSISTENT else
+                           "captured graph, one launch per kernel and order") + ")",
                        "tiles_elements_per_cta_p2_to_p5": choice, "dt": sh.dt,
                        "orders_schedule": ("one after another", "concurrent streams", "one persistent launch per stage")[b.schedule()],
                        "l2": "inputs larger than L2 (state %.0f MB)" % (state_bytes / 1e6),
@@ -423,13 +430,15 @@ def main():
     ap.add_argument("--ref-elems", type=int, default=256)
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--workload", default=None, choices=["batch_64"])
+    ap.add_argument("--workload", default=None, choices=["batch_64", "batch_16"])
+    ap.add_argument("--schedule", default="auto", choices=["auto", "serial", "concurrent", "persistent"],
+                    help="batch workloads: the step schedule (auto: the autotuner's choice)")
     ap.add_argument("--closure", action="store_true",
                     help="attach a seeded learned-closure record (p = 2 shells): every stage adds the network")
     args = ap.parse_args()
     cfg = CONFIGS[args.config]
     rank, world, local = _dist()
-    if args.workload == "batch_64" and args.impl == "chorus":
+    if args.workload in ("batch_64", "batch_16") and args.impl == "chorus":
         run_batch(args, rank, world, local)
         return
 

@@ -257,6 +257,10 @@ class BatchConfig:
 # 64 shells of the shell_288_p3 family (beta 0.75, 3 density scale heights), n 8-32, n_r 4-16, p 2-5
 BATCH_64 = BatchConfig("batch_64", 64, 4, 8, 32, 4, 16, (2, 3, 4, 5), 0.75, 1.0, 1e-3,
                        make_phys(0.75, 1.5, 3.0, 1e-3))
+# the same family at a quarter of the size (16 shells, 8-16 cells per panel edge, 4-8 layers): a
+# batch whose kernels a profiler captures in seconds
+BATCH_16 = BatchConfig("batch_16", 16, 4, 8, 16, 4, 8, (2, 3, 4, 5), 0.75, 1.0, 1e-3,
+                       make_phys(0.75, 1.5, 3.0, 1e-3))
 
 
 def small_batch() -> BatchConfig:
