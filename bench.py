@@ -558,6 +558,8 @@ def main():
     # pinned host memory, steps, and copies it back (chorus_rk_step_host)
     host = torch.empty(shape, dtype=tdt, pin_memory=True)
     host.copy_(Q)
+    if args.e2e_steps > 0:  # one untimed call: its copy stream and events are created on first use
+        mesh.rk_step_host(sh.params, prec, host, Q, ws, sh.dt, 1)
     torch.cuda.synchronize()
     t0 = time.perf_counter()
     for _ in range(args.e2e_steps):

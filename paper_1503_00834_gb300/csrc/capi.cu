@@ -405,6 +405,9 @@ cudaError_t timed(chorus_mesh_s* m, int cls, cudaStream_t st, Fn&& fn) {
 }
 
 void free_mesh(chorus_mesh_s* m) {
+  for (cudaEvent_t& e : m->copy_ev)
+    if (e) cudaEventDestroy(e);
+  if (m->copy_stream) cudaStreamDestroy(m->copy_stream);
   dev_free(m->closure_buf);
   release_records(m);
   for (cudaEvent_t e : m->pool) cudaEventDestroy(e);
@@ -925,6 +928,93 @@ chorus_status run_rk(chorus_mesh_s* m, R* u, const Ws<R>& w, double dt, int64_t 
   return CHORUS_OK;
 }
 
+// Chunks of the last stage's residual in chorus_rk_step_host (FP32).
+constexpr int kHostChunks = 4;
+
+// The residual kernel's per-element arguments shifted to elements [e0, e0 + ne): with the face kernel
+// the residual kernel reads no neighbour data (the common face fluxes are in each element's own face
+// numbering), so a range of elements is a mesh of its own for it.
+MeshArg<float> mesh_range(MeshArg<float> a, int64_t e0, int64_t ne, int N) {
+  const int64_t N2 = N * N, N3 = N2 * N;
+  a.E = (int)ne;
+  a.nbr += e0 * 6;
+  a.code += e0 * 6;
+  a.Sf += e0 * 9 * (N + 1) * N2;
+  a.invJ += e0 * N3;
+  a.x += e0 * 3 * N3;
+  if (a.kr) a.kr += e0 * 3 * (N + 1) * N2;
+  return a;
+}
+BgArg bg_range(BgArg b, int64_t e0, int N) {
+  const int64_t N2 = N * N, N3 = N2 * N;
+  b.bg += e0 * 2 * N3;
+  b.grho0 += e0 * 3 * N3;
+  b.bgT += e0 * 12 * N2;
+  if (b.R0) b.R0 += e0 * 5 * N3;
+  return b;
+}
+
+// chorus_rk_step_host, FP32 perturbation form: the state is already being copied in on st; the last
+// stage's residual runs in kHostChunks element ranges, and each range's new state is copied to the
+// host on the mesh's copy stream while the next range is computed.  Synchronises.
+chorus_status rk_step_host_fp32(chorus_mesh_s* m, const chorus_params& P, float* Qh, float* Qd, void* workspace,
+                                double dt, int64_t n_steps, cudaStream_t st) {
+  if (!m->prepared || !same_params(m->prep, P)) return CHORUS_EINVAL;
+  const chorus_status ks = ensure_kr(m, P, st);
+  if (ks != CHORUS_OK) return ks;
+  if (!m->copy_stream) {
+    CHK(cudaStreamCreateWithFlags(&m->copy_stream, cudaStreamNonBlocking));
+    for (cudaEvent_t& e : m->copy_ev) CHK(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
+  }
+  const PhysArg<float> ph = phys_arg<float>(P, m->r_inner, m->r_outer);
+  const MeshArg<float> ma = mesh_arg<float>(m);
+  const BgArg bg = bg_arg(m);
+  Ws<float> w = split_ws<float>(m, workspace);
+  const int N = m->N;
+  const int64_t N2 = N * N, N3 = N2 * N;
+  const int64_t last = n_steps * (int64_t)stages_of(0).size();
+  int64_t stage = 0;
+  bool copied = false;  // the chunks of the last stage copied the state out
+  const chorus_status s = run_rk<float>(
+      m, Qd, w, dt, n_steps, 0, st,
+      [&](const float* q, const float* T) {
+        return m->L.grad32(ma, m->ops32, ph, bg, q, T, w.Tv, w.G, w.Fc, m->d_err, st);
+      },
+      [&](const float* T) { return m->L.face32(ma, ph, bg, m->d_faces, m->n_ifaces, m->n_wfaces, T, w.Tv, w.Fc, st); },
+      [&](const float* q, const float* T, float* dst, float* Tn, const RkCoef<float>& c) -> cudaError_t {
+        if (++stage < last || dst != Qd)
+          return m->L.resid32(ma, m->ops32, ph, bg, q, T, w.Tv, w.G, w.Fc, dst, Tn, c, (float)dt, kModeRK, m->d_err, st);
+        for (int k = 0; k < kHostChunks; ++k) {
+          const int64_t e0 = m->E * k / kHostChunks, ne = m->E * (k + 1) / kHostChunks - e0;
+          if (ne == 0) continue;
+          RkCoef<float> ck = c;
+          const int64_t o5 = e0 * 5 * N3;
+          ck.un = c.un ? c.un + o5 : nullptr;
+          ck.un2 = c.un2 ? c.un2 + o5 : nullptr;
+          ck.out2 = c.out2 ? c.out2 + o5 : nullptr;
+          ck.radd = c.radd ? c.radd + o5 : nullptr;
+          cudaError_t e = m->L.resid32(mesh_range(ma, e0, ne, N), m->ops32, ph, bg_range(bg, e0, N), q + o5, T + e0 * 30 * N2,
+                                       w.Tv + e0 * 24 * N2, w.G + e0 * 12 * N3, w.Fc + e0 * 30 * N2, dst + o5,
+                                       Tn + e0 * 30 * N2, ck, (float)dt, kModeRK, m->d_err, st);
+          if (e == cudaSuccess) e = cudaEventRecord(m->copy_ev[k], st);
+          if (e == cudaSuccess) e = cudaStreamWaitEvent(m->copy_stream, m->copy_ev[k], 0);
+          if (e == cudaSuccess)
+            e = cudaMemcpyAsync(Qh + o5, dst + o5, ne * 5 * N3 * sizeof(float), cudaMemcpyDeviceToHost, m->copy_stream);
+          if (e != cudaSuccess) return e;
+        }
+        cudaError_t e = cudaEventRecord(m->copy_ev[kHostChunks], m->copy_stream);
+        if (e == cudaSuccess) e = cudaStreamWaitEvent(st, m->copy_ev[kHostChunks], 0);
+        copied = e == cudaSuccess;
+        return e;
+      },
+      [&](const float* q, float* T) { return m->L.trace32(ma, m->ops32, q, T, st); });
+  if (s != CHORUS_OK) return s;
+  if (!copied)  // a scheme whose last stage does not write the caller's state: one copy after it
+    CHK(cudaMemcpyAsync(Qh, Qd, (size_t)m->E * 5 * N3 * sizeof(float), cudaMemcpyDeviceToHost, st));
+  CHK(cudaStreamSynchronize(st));
+  return CHORUS_OK;
+}
+
 }  // namespace
 
 extern "C" {
@@ -985,6 +1075,11 @@ chorus_status chorus_rk_step_host(chorus_mesh m, const chorus_params* P, chorus_
   const size_t bytes = (size_t)m->E * 5 * m->N * m->N * m->N * (prec == CHORUS_FP64 ? sizeof(double) : sizeof(float));
   cudaStream_t st = (cudaStream_t)stream;
   CHK(cudaMemcpyAsync(Q_dev, Q_host, bytes, cudaMemcpyHostToDevice, st));
+  if (prec == CHORUS_FP32_PERT && n_steps > 0 && P && workspace && dt > 0.0 && std::isfinite(dt)) {
+    // the last stage's residual in element chunks, each chunk's state copied out while the next is
+    // computed (synchronises)
+    return rk_step_host_fp32(m, *P, (float*)Q_host, (float*)Q_dev, workspace, dt, n_steps, st);
+  }
   const chorus_status s = chorus_rk_step_scheme(m, P, prec, 0, Q_dev, workspace, dt, n_steps, stream);
   if (s != CHORUS_OK) return s;
   CHK(cudaMemcpyAsync(Q_host, Q_dev, bytes, cudaMemcpyDeviceToHost, st));

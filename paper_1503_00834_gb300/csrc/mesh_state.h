@@ -62,6 +62,9 @@ struct chorus_mesh_s {
   bool well_balanced = false;
   const void* closure = nullptr;
   void* closure_buf = nullptr;
+  // chorus_rk_step_host: the copy-out stream and the events of the last stage's element chunks
+  cudaStream_t copy_stream = nullptr;
+  cudaEvent_t copy_ev[5] = {nullptr, nullptr, nullptr, nullptr, nullptr};
 };
 
 namespace chorus {

@@ -437,7 +437,9 @@ def closure_apply(coarse: "Mesh", prec: int, w, Q, R, stream=None) -> None:
 
 
 def closure_attach(coarse: "Mesh", w) -> None:
+    """Attach the closure record w to the mesh (None detaches it); the mesh keeps a reference to w."""
     _ok("chorus_closure_attach", load().chorus_closure_attach(coarse.handle, None if w is None else _ptr(w)))
+    coarse._closure_record = w
 
 
 def afb_profile(params: Params, r_inner: float, r_outer: float, n: int = 16385, margin: float = 0.05):
