@@ -174,9 +174,10 @@ chorus_status chorus_rk_step(chorus_mesh mesh, const chorus_params* params, chor
  * full copy bandwidth) to Q_dev (device, caller-owned, same size), takes n_steps SSP-RK3 steps there,
  * copies the result back into Q_host and synchronises the stream.  workspace as for chorus_rk_step.
  * This is the end-to-end form of a step for callers whose state lives on the host.  In the FP32 form
- * the last stage's residual runs in four element ranges and each range's new state is copied back
- * (on a stream of the mesh's own) while the next range is computed; the result equals chorus_rk_step's
- * bit for bit.  Calls on one mesh must not overlap. */
+ * the state is copied in by eight element ranges (on a stream of the mesh's own, after the work
+ * already queued on `stream`), each range's face traces computed as soon as it has arrived, and the
+ * last stage's residual runs on the same ranges, each range's new state copied back while the next is
+ * computed; the result equals chorus_rk_step's bit for bit.  Calls on one mesh must not overlap. */
 chorus_status chorus_rk_step_host(chorus_mesh mesh, const chorus_params* params, chorus_precision prec,
                                   void* Q_host, void* Q_dev, void* workspace, double dt, int64_t n_steps,
                                   void* stream);

@@ -928,8 +928,9 @@ chorus_status run_rk(chorus_mesh_s* m, R* u, const Ws<R>& w, double dt, int64_t 
   return CHORUS_OK;
 }
 
-// Chunks of the last stage's residual in chorus_rk_step_host (FP32).
-constexpr int kHostChunks = 4;
+// Element chunks of chorus_rk_step_host (FP32): the copy in with the traces, the last stage's residual
+// with the copy out.
+constexpr int kHostChunks = 8;
 
 // The residual kernel's per-element arguments shifted to elements [e0, e0 + ne): with the face kernel
 // the residual kernel reads no neighbour data (the common face fluxes are in each element's own face
@@ -954,9 +955,10 @@ BgArg bg_range(BgArg b, int64_t e0, int N) {
   return b;
 }
 
-// chorus_rk_step_host, FP32 perturbation form: the state is already being copied in on st; the last
-// stage's residual runs in kHostChunks element ranges, and each range's new state is copied to the
-// host on the mesh's copy stream while the next range is computed.  Synchronises.
+// chorus_rk_step_host, FP32 perturbation form: the state is copied in in kHostChunks element ranges
+// on the mesh's copy stream, each range's traces computed as soon as it has arrived; the last stage's
+// residual runs on the same ranges, and each range's new state is copied to the host while the next
+// range is computed.  Synchronises.
 chorus_status rk_step_host_fp32(chorus_mesh_s* m, const chorus_params& P, float* Qh, float* Qd, void* workspace,
                                 double dt, int64_t n_steps, cudaStream_t st) {
   if (!m->prepared || !same_params(m->prep, P)) return CHORUS_EINVAL;
@@ -966,6 +968,12 @@ chorus_status rk_step_host_fp32(chorus_mesh_s* m, const chorus_params& P, float*
     CHK(cudaStreamCreateWithFlags(&m->copy_stream, cudaStreamNonBlocking));
     for (cudaEvent_t& e : m->copy_ev) CHK(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
   }
+  static_assert(2 * kHostChunks + 2 <= (int)(sizeof(m->copy_ev) / sizeof(cudaEvent_t)), "events per chunk");
+  cudaEvent_t* ev_in = m->copy_ev + kHostChunks + 1;  // [kHostChunks + 1]: the start, then one per range in
+  auto range = [&](int k, int64_t* e0, int64_t* ne) {
+    *e0 = m->E * k / kHostChunks;
+    *ne = m->E * (k + 1) / kHostChunks - *e0;
+  };
   const PhysArg<float> ph = phys_arg<float>(P, m->r_inner, m->r_outer);
   const MeshArg<float> ma = mesh_arg<float>(m);
   const BgArg bg = bg_arg(m);
@@ -985,7 +993,8 @@ chorus_status rk_step_host_fp32(chorus_mesh_s* m, const chorus_params& P, float*
         if (++stage < last || dst != Qd)
           return m->L.resid32(ma, m->ops32, ph, bg, q, T, w.Tv, w.G, w.Fc, dst, Tn, c, (float)dt, kModeRK, m->d_err, st);
         for (int k = 0; k < kHostChunks; ++k) {
-          const int64_t e0 = m->E * k / kHostChunks, ne = m->E * (k + 1) / kHostChunks - e0;
+          int64_t e0, ne;
+          range(k, &e0, &ne);
           if (ne == 0) continue;
           RkCoef<float> ck = c;
           const int64_t o5 = e0 * 5 * N3;
@@ -1007,7 +1016,23 @@ chorus_status rk_step_host_fp32(chorus_mesh_s* m, const chorus_params& P, float*
         copied = e == cudaSuccess;
         return e;
       },
-      [&](const float* q, float* T) { return m->L.trace32(ma, m->ops32, q, T, st); });
+      [&](const float* q, float* T) -> cudaError_t {
+        // the copy in, range by range on the copy stream (after the caller's earlier work on st), and
+        // each range's traces once it has arrived
+        cudaError_t e = cudaEventRecord(ev_in[kHostChunks], st);
+        if (e == cudaSuccess) e = cudaStreamWaitEvent(m->copy_stream, ev_in[kHostChunks], 0);
+        for (int k = 0; k < kHostChunks && e == cudaSuccess; ++k) {
+          int64_t e0, ne;
+          range(k, &e0, &ne);
+          if (ne == 0) continue;
+          const int64_t o5 = e0 * 5 * N3;
+          e = cudaMemcpyAsync(Qd + o5, Qh + o5, ne * 5 * N3 * sizeof(float), cudaMemcpyHostToDevice, m->copy_stream);
+          if (e == cudaSuccess) e = cudaEventRecord(ev_in[k], m->copy_stream);
+          if (e == cudaSuccess) e = cudaStreamWaitEvent(st, ev_in[k], 0);
+          if (e == cudaSuccess) e = m->L.trace32(mesh_range(ma, e0, ne, N), m->ops32, q + o5, T + e0 * 30 * N2, st);
+        }
+        return e;
+      });
   if (s != CHORUS_OK) return s;
   if (!copied)  // a scheme whose last stage does not write the caller's state: one copy after it
     CHK(cudaMemcpyAsync(Qh, Qd, (size_t)m->E * 5 * N3 * sizeof(float), cudaMemcpyDeviceToHost, st));
@@ -1074,12 +1099,12 @@ chorus_status chorus_rk_step_host(chorus_mesh m, const chorus_params* P, chorus_
   if (!m || !Q_host || !Q_dev || (prec != CHORUS_FP64 && prec != CHORUS_FP32_PERT)) return CHORUS_EINVAL;
   const size_t bytes = (size_t)m->E * 5 * m->N * m->N * m->N * (prec == CHORUS_FP64 ? sizeof(double) : sizeof(float));
   cudaStream_t st = (cudaStream_t)stream;
-  CHK(cudaMemcpyAsync(Q_dev, Q_host, bytes, cudaMemcpyHostToDevice, st));
   if (prec == CHORUS_FP32_PERT && n_steps > 0 && P && workspace && dt > 0.0 && std::isfinite(dt)) {
-    // the last stage's residual in element chunks, each chunk's state copied out while the next is
-    // computed (synchronises)
+    // copies in element chunks overlapping the first traces and the last stage's residual
+    // (synchronises)
     return rk_step_host_fp32(m, *P, (float*)Q_host, (float*)Q_dev, workspace, dt, n_steps, st);
   }
+  CHK(cudaMemcpyAsync(Q_dev, Q_host, bytes, cudaMemcpyHostToDevice, st));
   const chorus_status s = chorus_rk_step_scheme(m, P, prec, 0, Q_dev, workspace, dt, n_steps, stream);
   if (s != CHORUS_OK) return s;
   CHK(cudaMemcpyAsync(Q_host, Q_dev, bytes, cudaMemcpyDeviceToHost, st));

@@ -62,9 +62,9 @@ struct chorus_mesh_s {
   bool well_balanced = false;
   const void* closure = nullptr;
   void* closure_buf = nullptr;
-  // chorus_rk_step_host: the copy-out stream and the events of the last stage's element chunks
+  // chorus_rk_step_host: the copy stream and the events of its element chunks (in and out)
   cudaStream_t copy_stream = nullptr;
-  cudaEvent_t copy_ev[5] = {nullptr, nullptr, nullptr, nullptr, nullptr};
+  cudaEvent_t copy_ev[18] = {};
 };
 
 namespace chorus {
