@@ -346,19 +346,18 @@ def run_batch(args, rank, world, local):
     alg = sum(e * (p + 1) ** 3 * ALG_BYTES_PER_DOF_STAGE[p] for e, p in zip(b.n_elem, b.orders))
     peak, peak_kind = _peaks()
     achieved = alg / (ms / stages / 1e3) / 1e9
-    # end to end: H2D of the whole batch state, one step, D2H of the state
+    # end to end through chorus_batch_rk_step_host: every step copies each order's state in from
+    # pinned host memory, steps it and copies it back, the orders pipelined
     host = torch.empty(Q.shape, dtype=Q.dtype, pin_memory=True)
     host.copy_(Q)
-    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    if args.e2e_steps > 0:  # one untimed call: its copy streams and events are created on first use
+        b.rk_step_host(host, Q, ws, sh.dt, 1)
     torch.cuda.synchronize()
-    e0.record(stream)
+    t0 = time.perf_counter()
     for _ in range(args.e2e_steps):
-        Q.copy_(host, non_blocking=True)
-        b.rk_step(Q, ws, sh.dt, 1)
-        host.copy_(Q, non_blocking=True)
-    e1.record(stream)
-    torch.cuda.synchronize()
-    e2e_value = world * n_dof * 3 * args.e2e_steps / (e0.elapsed_time(e1) / 1e3)
+        b.rk_step_host(host, Q, ws, sh.dt, 1)
+    e2e_s = max(time.perf_counter() - t0, 1e-9)
+    e2e_value = world * n_dof * 3 * args.e2e_steps / e2e_s
     state_bytes = Q.numel() * Q.element_size()
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
@@ -386,7 +385,7 @@ def run_batch(args, rank, world, local):
             "gpu_launches": int(launches * args.steps),
             "clocks": clocks,
             "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": state_bytes,
-                    "d2h_bytes_per_step": state_bytes},
+                    "d2h_bytes_per_step": state_bytes, "call": "chorus_batch_rk_step_host (host state in and out)"},
             "cpu_baseline": cpu,
             "mass_total": float(red[:, 0].sum()),
         }))

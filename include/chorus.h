@@ -365,6 +365,16 @@ chorus_status chorus_batch_init(chorus_batch batch, float* Q, void* stream);
 chorus_status chorus_batch_rk_step(chorus_batch batch, float* Q, void* workspace, double dt, int64_t n_steps,
                                    void* stream, int64_t* launches);
 
+/* chorus_batch_rk_step on a batch state held in host memory (Q_host: host, the batch layout, pinned
+ * for full copy bandwidth; Q_dev: device, caller-owned, n_state floats): each order's state is copied
+ * in, stepped n_steps times and copied back, the orders pipelined (the copy in of one order and the
+ * copy out of another overlap the steps of a third; the smallest state first) on copy streams of
+ * the batch's own; the kernels are the per-order ones, one order after another, so the result
+ * equals chorus_batch_rk_step's with the serial schedule bit for bit.  Synchronises; calls on one
+ * batch must not overlap. */
+chorus_status chorus_batch_rk_step_host(chorus_batch batch, float* Q_host, float* Q_dev, void* workspace, double dt,
+                                        int64_t n_steps, void* stream);
+
 /* Per-shell FP64 reductions of the total state as chorus_reduce: out host double[n_shells][4]
  * (mass, total energy, kinetic energy, |L|).  Synchronises. */
 chorus_status chorus_batch_reduce(chorus_batch batch, const float* Q, double* out, void* stream);

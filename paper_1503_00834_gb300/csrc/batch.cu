@@ -42,6 +42,9 @@ struct chorus_batch_s {
   bool concurrent = true;  // orders on forked streams (true) or one after another (false)
   bool persistent = false;  // one persistent launch per RK stage for all orders (overrides concurrent)
   unsigned* d_sync = nullptr;  // the persistent launch's grid-barrier and work counters
+  // chorus_batch_rk_step_host: the copy-in and copy-out streams and their events
+  cudaStream_t in_stream = nullptr, out_stream = nullptr;
+  std::vector<cudaEvent_t> host_ev;
   cudaGraphExec_t exec = nullptr;
   const float* g_Q = nullptr;
   const void* g_ws = nullptr;
@@ -70,6 +73,9 @@ void free_batch(chorus_batch_s* b) {
   if (b->fork) cudaEventDestroy(b->fork);
   if (b->cap) cudaStreamDestroy(b->cap);
   if (b->d_sync) cudaFree(b->d_sync);
+  for (cudaEvent_t e : b->host_ev) cudaEventDestroy(e);
+  if (b->in_stream) cudaStreamDestroy(b->in_stream);
+  if (b->out_stream) cudaStreamDestroy(b->out_stream);
   delete b;
 }
 
@@ -297,6 +303,59 @@ chorus_status chorus_batch_rk_step(chorus_batch b, float* Q, void* workspace, do
   for (int64_t n = 0; n < n_steps; ++n)
     if (cudaGraphLaunch(b->exec, st) != cudaSuccess) return CHORUS_ECUDA;
   return CHORUS_OK;
+}
+
+chorus_status chorus_batch_rk_step_host(chorus_batch b, float* Q_host, float* Q_dev, void* workspace, double dt,
+                                        int64_t n_steps, void* stream) {
+  if (!b || !Q_host || !Q_dev || !workspace || !(dt > 0.0) || !std::isfinite(dt) || n_steps < 0) return CHORUS_EINVAL;
+  cudaStream_t st = (cudaStream_t)stream;
+  const size_t ng = b->groups.size();
+  if (!b->in_stream) {
+    if (cudaStreamCreateWithFlags(&b->in_stream, cudaStreamNonBlocking) != cudaSuccess ||
+        cudaStreamCreateWithFlags(&b->out_stream, cudaStreamNonBlocking) != cudaSuccess)
+      return CHORUS_ECUDA;
+    b->host_ev.assign(2 * ng + 2, nullptr);
+    for (cudaEvent_t& e : b->host_ev)
+      if (cudaEventCreateWithFlags(&e, cudaEventDisableTiming) != cudaSuccess) return CHORUS_ECUDA;
+  }
+  auto bytes_of = [&](size_t g) {
+    const int N = b->groups[g].p + 1;
+    return (size_t)b->groups[g].mesh->E * 5 * N * N * N * sizeof(float);
+  };
+  // the order of the groups: the smallest state first (its copy in is not overlapped), then from the
+  // largest down, the second smallest last (its copy out is not overlapped)
+  std::vector<size_t> ord(ng);
+  for (size_t g = 0; g < ng; ++g) ord[g] = g;
+  std::sort(ord.begin(), ord.end(), [&](size_t x, size_t y) { return bytes_of(x) < bytes_of(y); });
+  if (ng > 2) std::reverse(ord.begin() + 1, ord.end());
+  cudaEvent_t* ev_in = b->host_ev.data();
+  cudaEvent_t* ev_done = ev_in + ng;
+  cudaEvent_t start = ev_in[2 * ng], end = ev_in[2 * ng + 1];
+  auto cu = [](cudaError_t e) { return e == cudaSuccess ? CHORUS_OK : CHORUS_ECUDA; };
+  chorus_status s = cu(cudaEventRecord(start, st));  // after the caller's earlier work on st
+  if (s == CHORUS_OK) s = cu(cudaStreamWaitEvent(b->in_stream, start, 0));
+  for (size_t i = 0; i < ng && s == CHORUS_OK; ++i) {  // every copy in, one after another
+    const auto& g = b->groups[ord[i]];
+    s = cu(cudaMemcpyAsync(Q_dev + g.state_off, Q_host + g.state_off, bytes_of(ord[i]), cudaMemcpyHostToDevice,
+                           b->in_stream));
+    if (s == CHORUS_OK) s = cu(cudaEventRecord(ev_in[i], b->in_stream));
+  }
+  for (size_t i = 0; i < ng && s == CHORUS_OK; ++i) {  // each group's steps once its state is in
+    const auto& g = b->groups[ord[i]];
+    s = cu(cudaStreamWaitEvent(st, ev_in[i], 0));
+    if (s == CHORUS_OK)
+      s = chorus_rk_step_scheme(g.mesh, &b->params, CHORUS_FP32_PERT, 0, Q_dev + g.state_off, (char*)workspace + g.ws_off,
+                                dt, n_steps, st);
+    if (s == CHORUS_OK) s = cu(cudaEventRecord(ev_done[i], st));
+    if (s == CHORUS_OK) s = cu(cudaStreamWaitEvent(b->out_stream, ev_done[i], 0));
+    if (s == CHORUS_OK)
+      s = cu(cudaMemcpyAsync(Q_host + g.state_off, Q_dev + g.state_off, bytes_of(ord[i]), cudaMemcpyDeviceToHost,
+                             b->out_stream));
+  }
+  if (s == CHORUS_OK) s = cu(cudaEventRecord(end, b->out_stream));
+  if (s == CHORUS_OK) s = cu(cudaStreamWaitEvent(st, end, 0));
+  if (s == CHORUS_OK) s = cu(cudaStreamSynchronize(st));
+  return s;
 }
 
 chorus_status chorus_batch_reduce(chorus_batch b, const float* Q, double* out, void* stream) {

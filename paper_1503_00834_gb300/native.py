@@ -32,7 +32,7 @@ EXPORTS = ("chorus_mesh_create", "chorus_mesh_destroy", "chorus_mesh_info", "cho
            "chorus_batch_reduce", "chorus_batch_autotune", "chorus_set_well_balanced", "chorus_prepare_profile",
            "chorus_afb_profile", "chorus_closure_set_scales", "chorus_stable_dt_rule", "chorus_stable_dt",
            "chorus_set_wait_limit", "chorus_fma_rate", "chorus_rk_step_host", "chorus_batch_schedule",
-           "chorus_batch_set_wait_limit")
+           "chorus_batch_set_wait_limit", "chorus_batch_rk_step_host")
 
 
 class ChorusError(RuntimeError):
@@ -126,6 +126,7 @@ def load() -> ctypes.CDLL:
         "chorus_rk_step_host": (i32, [vp, P(Params), i32, vp, vp, vp, f64, i64, vp]),
         "chorus_batch_schedule": (i32, [vp, i32, P(i32)]),
         "chorus_batch_set_wait_limit": (i32, [vp, i64]),
+        "chorus_batch_rk_step_host": (i32, [vp, vp, vp, vp, f64, i64, vp]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(lib, name)
@@ -345,6 +346,14 @@ class Batch:
         _ok("chorus_batch_rk_step", load().chorus_batch_rk_step(self.handle, _ptr(Q), _ptr(ws), dt, n_steps,
                                                                 _stream(stream), ctypes.byref(n)))
         return n.value
+
+    def rk_step_host(self, Q_host, Q_dev, ws, dt: float, n_steps: int, stream=None) -> None:
+        """n_steps SSP-RK3 steps of a host-resident batch state (contiguous CPU tensor, pinned for full
+        bandwidth), the orders' copies pipelined with their steps; synchronises."""
+        if Q_host.is_cuda or not Q_host.is_contiguous():
+            raise ValueError("Q_host must be a contiguous host tensor")
+        _ok("chorus_batch_rk_step_host", load().chorus_batch_rk_step_host(
+            self.handle, ctypes.c_void_p(Q_host.data_ptr()), _ptr(Q_dev), _ptr(ws), dt, n_steps, _stream(stream)))
 
     def reduce(self, Q, stream=None) -> np.ndarray:
         out = (ctypes.c_double * (4 * len(self.orders)))()

@@ -217,3 +217,26 @@ def test_persistent_barrier_timeout_is_reported_and_stores_nothing(batch):
         assert torch.equal(Q, Q1) and not torch.equal(Q1, Q0)
     finally:
         b.schedule(was)
+
+
+def test_host_step_equals_device_step(batch):
+    """chorus_batch_rk_step_host (the orders' copies pipelined with their steps) against the graph
+    step with the orders one after another, on the same initial state: every shell bit-identical."""
+    b = batch.batch
+    was = b.schedule()
+    try:
+        b.schedule(b.SERIAL)
+        Q, ws = _alloc(batch)
+        b.init(Q)
+        host = torch.empty(Q.shape, dtype=Q.dtype, pin_memory=True)
+        host.copy_(Q)
+        Q_dev = torch.empty_like(Q)
+        b.rk_step_host(host, Q_dev, ws, batch.dt, 2)
+        b.rk_step(Q, ws, batch.dt, 2)
+        torch.cuda.synchronize()
+        assert np.all(np.isfinite(b.reduce(Q)))
+        Qc = Q.cpu()
+        for s in range(len(batch.cfgs)):
+            assert torch.equal(b.view(host, s), b.view(Qc, s)), s
+    finally:
+        b.schedule(was)
